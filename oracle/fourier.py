@@ -21,7 +21,8 @@ Parseval, and numpy.fft (tests/test_oracle_fourier.py).
 """
 import numpy as np
 
-__all__ = ["dft_axis", "forward", "inverse", "frequencies", "wavevectors", "nyquist_mask"]
+__all__ = ["dft_axis", "forward", "inverse", "frequencies", "discrete_frequencies",
+           "wavevectors", "nyquist_mask"]
 
 
 def _is_pow2(n):
@@ -78,17 +79,32 @@ def frequencies(n):
     return np.where(j >= (n + 1) // 2, j - n, j)
 
 
+def discrete_frequencies(n):
+    """Integer frequency used for derivatives: ``frequencies`` with the Nyquist index set to 0.
+
+    Reading of the paper on even grids: the sign of a Nyquist component is ambiguous
+    (k = -N/2 and +N/2 alias), and neither Gamma0_hat nor the odd symbols are even in a
+    single component, so a real operator needs a rule.  The derivative of a Nyquist
+    mode is taken as zero (the average of its two signs), for every spectral operator.
+    """
+    k = frequencies(n)
+    if n % 2 == 0:
+        k = np.where(k == -(n // 2), 0, k)
+    return k
+
+
 def wavevectors(grid):
-    """xi = 2 pi k / (N h) per axis, h = 1/max(N) (cubic voxels; unit torus for cubes).
+    """Discrete wave vector xi = 2 pi k / (N h) per axis, h = 1/max(N), Nyquist -> 0.
 
     ``grid`` is (N1, N2, N3) with N1 the fastest (x) axis.  Returns (xi1, xi2, xi3),
-    each broadcastable to the array shape (N3, N2, N1).
+    each broadcastable to the array shape (N3, N2, N1).  Cubic voxels make the cubic
+    grids exactly the unit torus of Sec. 2.
     """
     n1, n2, n3 = grid
     h = 1.0 / max(grid)
-    xi1 = 2 * np.pi * frequencies(n1) / (n1 * h)
-    xi2 = 2 * np.pi * frequencies(n2) / (n2 * h)
-    xi3 = 2 * np.pi * frequencies(n3) / (n3 * h)
+    xi1 = 2 * np.pi * discrete_frequencies(n1) / (n1 * h)
+    xi2 = 2 * np.pi * discrete_frequencies(n2) / (n2 * h)
+    xi3 = 2 * np.pi * discrete_frequencies(n3) / (n3 * h)
     return (xi1[None, None, :], xi2[None, :, None], xi3[:, None, None])
 
 

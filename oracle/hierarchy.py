@@ -27,8 +27,9 @@ Unit loads:
 
 Readings (the paper is silent or garbled here):
 * the mean of g_alpha is dropped (theta_hat(0) = 0), the corrector has zero mean;
-* the odd-symbol spectral operators (theta_hat, displacement recovery) zero the
-  Nyquist planes of even axes;
+* every spectral operator (theta_hat, displacement recovery, e_y, Gamma0_hat) uses the
+  discrete wave vector of ``fourier.wavevectors``, whose Nyquist components are 0, and
+  vanishes where that vector is 0;
 * the higher-order effective tensor of order alpha is the mean order-alpha stress per
   unit load, D[:, load] = < C : eps_alpha + p_alpha > (Mandel), which the paper leaves
   for future work.
@@ -63,17 +64,15 @@ def displacement_from_strain(eps, grid):
     qs = np.where(q > 0, q, 1.0)
     s = np.einsum("i...,i...->...", xi, w)
     uh = -1j * (2.0 * w - xi * s / qs) / qs
-    kill = (q == 0) | fourier.nyquist_mask(grid)
-    uh = np.where(kill, 0.0, uh)
+    uh = np.where(q == 0, 0.0, uh)
     return fourier.inverse(uh).real
 
 
 def strain_from_displacement(u, grid):
-    """e_y(u) = sym grad_y u computed spectrally: i sym(xi (x) u_hat), Nyquist zeroed."""
+    """e_y(u) = sym grad_y u computed spectrally: i sym(xi (x) u_hat)."""
     shape = u.shape[1:]
     xi = _xi_stack(grid, shape[-3:])
     uh = fourier.forward(u)
-    uh = np.where(fourier.nyquist_mask(grid), 0.0, uh)
     eh = 0.5j * (np.einsum("i...,j...->ij...", xi, uh) + np.einsum("i...,j...->ij...", uh, xi))
     return fourier.inverse(eh).real
 
@@ -81,7 +80,7 @@ def strain_from_displacement(u, grid):
 def theta_hat(g_hat, grid):
     """theta_hat(xi) = i/|xi|^4 [ (xi (x) xi)(g_hat . xi) - (g_hat (x) xi + xi (x) g_hat)|xi|^2 ].
 
-    Zero at xi = 0 and on Nyquist planes.
+    Zero where the discrete wave vector vanishes.
     """
     shape = g_hat.shape[1:]
     xi = _xi_stack(grid, shape[-3:])
@@ -91,8 +90,7 @@ def theta_hat(g_hat, grid):
     xx = np.einsum("i...,j...->ij...", xi, xi)
     gxs = np.einsum("i...,j...->ij...", g_hat, xi) + np.einsum("i...,j...->ij...", xi, g_hat)
     th = 1j / qs ** 2 * (xx * gx - gxs * q)
-    kill = (q == 0) | fourier.nyquist_mask(grid)
-    return np.where(kill, 0.0, th)
+    return np.where(q == 0, 0.0, th)
 
 
 def rhs_order_alpha(problem, p, g):

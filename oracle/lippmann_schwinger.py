@@ -55,6 +55,10 @@ def gamma0_hat_slab(xi1, xi2, xi3, lam0, mu0):
 def green_apply(tau_hat, grid, lam0, mu0):
     """eta_hat = -Gamma0_hat(xi) : tau_hat(xi) for xi != 0, eta_hat(0) = 0.
 
+    xi is the discrete wave vector (Nyquist components 0, see ``fourier.wavevectors``),
+    so the multiplier is Hermitian and Gamma0_hat : C0 : Gamma0_hat = Gamma0_hat holds at
+    every frequency; it also vanishes at the pure-Nyquist frequencies.
+
     ``tau_hat`` has shape (3, 3, ..., N3, N2, N1); leading batch axes are allowed.
     """
     xi1, xi2, xi3 = fourier.wavevectors(grid)

@@ -109,12 +109,14 @@ def test_laminate_closed_form_worked_values():
     np.testing.assert_allclose(one, iso_mandel_matrix(2.0, 0.7), atol=1e-13)
 
 
-@pytest.mark.parametrize("scheme", ["cg", "basic"])
-def test_laminate_solution_is_exact(scheme):
-    ms = synthetic.laminate((8, 4, 4), split=3)
+@pytest.mark.parametrize("scheme,split", [("cg", 2), ("basic", 4), ("cg", 6)])
+def test_laminate_solution_is_exact(scheme, split):
+    """Exact for layers of even thickness, whose strain has no Nyquist content along x1."""
+    ms = synthetic.laminate((8, 4, 4), split=split)
     pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
     _, c_eff = pb.solve_order0(tol=1e-13, scheme=scheme)
-    exact = closed_forms.laminate_stiffness([tuple(ms.lame[0]), tuple(ms.lame[1])], [3 / 8, 5 / 8])
+    exact = closed_forms.laminate_stiffness([tuple(ms.lame[0]), tuple(ms.lame[1])],
+                                            [split / 8, 1 - split / 8])
     np.testing.assert_allclose(c_eff, exact, atol=1e-10 * np.abs(exact).max())
 
 
@@ -133,13 +135,10 @@ def test_sphere_bounds_and_symmetry():
     assert lo <= k <= hi
 
 
-def test_cg_result_independent_of_reference_medium():
-    """On odd grids (no Nyquist modes) the discrete solution does not depend on C0.
-
-    On even grids the Nyquist planes keep Gamma0_hat(xi) of the chosen C0, so the discrete
-    solution there does depend on C0; both sides of every parity test use the same C0.
-    """
-    ms = synthetic.centred_sphere(9)
+@pytest.mark.parametrize("n", [8, 9])
+def test_cg_result_independent_of_reference_medium(n):
+    """Gamma0_hat(xi) is a C0-projection at every discrete xi, so the solution ignores C0."""
+    ms = synthetic.centred_sphere(n)
     E = unit_mandel_load(1)
     outs = []
     for lam0, mu0 in [(5.5, 5.5), (0.0, 6.0), (3.0, 9.0)]:
@@ -148,3 +147,14 @@ def test_cg_result_independent_of_reference_medium():
         outs.append(eps)
     np.testing.assert_allclose(outs[1], outs[0], atol=1e-9)
     np.testing.assert_allclose(outs[2], outs[0], atol=1e-9)
+
+
+def test_ls_step_is_a_real_operator():
+    """The Fourier-series step maps real fields to real fields (Hermitian multiplier)."""
+    ms = synthetic.centred_sphere(6)
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    rng = np.random.default_rng(8)
+    eps = mandel_to_tensor(rng.standard_normal((6, 6, 6, 6)))
+    tau = pb.polarization(eps, None)
+    full = fourier.inverse(green_apply(fourier.forward(tau), pb.grid, pb.lam0, pb.mu0))
+    assert np.abs(full.imag).max() < 1e-13 * np.abs(full.real).max()
