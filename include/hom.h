@@ -1,0 +1,169 @@
+/*
+ * hom.h -- C ABI of libhom, an sm_103a (GB300) implementation of FFT-based
+ * homogenization with higher-order terms after Dietrich, Merkert and Simeon,
+ * "Derivation of higher-order terms in FFT-based numerical homogenization"
+ * (arXiv:1712.05145).
+ *
+ * The library solves, on one GPU, the periodic Lippmann-Schwinger equation of
+ * quasi-static linear elasticity on a voxel representative volume element
+ * (Sec. 2: Hooke's law, balance of momentum, polarization problem, Lippmann-
+ * Schwinger equation with the closed-form isotropic Green operator Gamma0_hat)
+ * with the Basic Scheme or its CG form (Algorithm 1, Eq. cg_form), and the
+ * generalized problems of order alpha of Sec. 3 (Definition of the generalized
+ * homogenization problem, theta_alpha closed form, modified initialization).
+ *
+ * Conventions shared by every entry point
+ *  - Grid (N1, N2, N3), N1 the fastest axis.  Cubic voxels of edge h = 1/max(N);
+ *    cubic grids are exactly the unit torus [-1/2, 1/2)^3 of Sec. 2.
+ *  - Scalar voxel arrays are [N3][N2][N1]; fields are [field][component][N3][N2][N1].
+ *  - Symmetric tensors are Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12);
+ *    vectors are 3 components (x1, x2, x3).  6x6 and 6xK matrices are row-major.
+ *  - Orders are counted from 0: order 0 is the classical cell problem (the paper's
+ *    alpha = 1), order 1 and 2 are the paper's alpha = 2 and alpha = 3.
+ *  - Unit loads: order 0, load A = 0..5 is the Mandel unit strain E^A; order 1,
+ *    load 3*A + k is E(Y) = E^A Y_k (18 loads); order 2, load 6*A + P is
+ *    E(Y) = E^A Y_k Y_l / (1 + delta_kl) with (k, l) the P-th Mandel pair (36 loads).
+ *  - Spectral operators use the discrete wave vector xi_i = 2 pi k_i / (N_i h) with the
+ *    Nyquist component (k_i = N_i/2 on even axes) taken as 0.
+ *  - Errors are returned as hom_status; no C++ exception crosses the ABI.  After an
+ *    error, hom_last_error(h) describes it.  A handle is used by one host thread at a
+ *    time; all its GPU work runs on the stream given in hom_options (default: a stream
+ *    the handle creates).
+ *  - Device pointers must be allocated on the device that was current at hom_create.
+ */
+#ifndef HOM_H
+#define HOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HOM_API __attribute__((visibility("default")))
+
+typedef struct hom_ctx* hom_t;
+
+typedef enum {
+  HOM_OK = 0,
+  HOM_ERR_ARG = 1,           /* invalid argument (null pointer, bad index, bad option) */
+  HOM_ERR_SIZE = 2,          /* grid axis not supported (see hom_create) */
+  HOM_ERR_NOMEM = 3,         /* device allocation failed */
+  HOM_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance */
+  HOM_ERR_ORDER = 5,         /* lower-order correctors missing */
+  HOM_ERR_NUMERIC = 6,       /* NaN or Inf met in a reduction */
+  HOM_ERR_TIMEOUT = 7,       /* a bounded device wait expired */
+  HOM_ERR_CUDA = 8           /* CUDA runtime error (text in hom_last_error) */
+} hom_status;
+
+enum { HOM_FP64 = 0, HOM_FP32_REFINE = 1 };
+enum { HOM_BASIC = 0, HOM_CG = 1 };
+enum { HOM_FIELD_STRAIN = 0, HOM_FIELD_DISPLACEMENT = 1, HOM_FIELD_STRESS = 2 };
+
+typedef struct {
+  int32_t precision;       /* HOM_FP64: FP64 fields and FFTs.  HOM_FP32_REFINE: FP32 fields and
+                              FFTs, FP64 reductions, FP64 residual-correction sweeps. */
+  int32_t scheme;          /* HOM_BASIC (fixed point) or HOM_CG (CG on A eps = b, C0 product) */
+  int32_t max_iter;        /* iteration cap per load (inner iterations in FP32_REFINE) */
+  int32_t check_every;     /* iterations between host convergence checks (>= 1) */
+  int32_t max_refine;      /* FP32_REFINE: cap on FP64 residual-correction sweeps */
+  int32_t rhs_chunk;       /* loads whose spectra are transformed per launch; 0 = choose so
+                              that the spectrum scratch fits l2_budget_bytes */
+  int64_t l2_budget_bytes; /* target size of the spectrum scratch (0 = 64 MiB) */
+  void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
+  int32_t reserved[8];
+} hom_options;
+
+typedef struct {
+  int32_t iterations;        /* iterations performed (inner iterations summed over sweeps) */
+  int32_t refinements;       /* FP64 residual-correction sweeps performed */
+  int32_t status;            /* hom_status of this load */
+  int32_t reserved;
+  double rel_residual;       /* last relative residual tracked by the iteration */
+  double rel_residual_fp64;  /* ||b - A eps||_L2 / ||b||_L2 recomputed in FP64 at the end */
+} hom_solve_info;
+
+/* Fills *opt with defaults: HOM_FP32_REFINE, HOM_CG, max_iter 2000, check_every 8,
+ * max_refine 6, rhs_chunk 0, l2_budget_bytes 64 MiB, own stream. */
+HOM_API void hom_default_options(hom_options* opt);
+
+/* Creates a handle for one voxel RVE (Sec. 2: C(x) piecewise isotropic, reference C0).
+ *  grid[3]     N1, N2, N3.  N1 even with N1/2, N2 and N3 in {2,3,4,6,8,12,16,24,32,48,64,96,
+ *              128,192,256,384,512}, and (N1/2) * N2 <= 8192 (one x-y plane per CTA).
+ *  phase       uint8 [N3][N2][N1], host or device pointer (auto-detected); copied.
+ *  n_phase     1..256; every phase index must be < n_phase.
+ *  lame        double [n_phase][2] host array of (lambda, mu) per phase; copied.
+ *  lambda0,mu0 Lame parameters of the reference medium C0 (mu0 != 0, lambda0+2mu0 != 0).
+ *  opt         options (NULL = defaults); the stream pointer is borrowed, not owned.
+ *  out         receives the handle (owned by the caller; release with hom_destroy).
+ * Allocates device memory for the RVE and the scratch; errors leave *out unset. */
+HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32_t n_phase,
+                              const double* lame, double lambda0, double mu0,
+                              const hom_options* opt, hom_t* out);
+
+/* Solves problem `order` (0, 1 or 2) for its loads to relative residual tol:
+ * ||b - A eps||_L2 / ||b||_L2 < tol with A = Id + Gamma0 * (C - C0) (Eq. cg_form); for the
+ * Basic Scheme this is the paper's Cauchy quantity ||eps_{n+1} - eps_n|| / ||eps_0||.
+ *  order 0: n_loads macroscopic strains, loads = double [n_loads][6] Mandel host array, or
+ *           loads = NULL for the 6 unit loads (n_loads ignored).  n_loads <= 64.
+ *  order 1: requires a converged order 0 with unit loads; loads must be NULL (18 loads).
+ *  order 2: requires order 1; loads must be NULL (36 loads).
+ *  info     host array of one hom_solve_info per load (nullable); caller-owned.
+ * The correctors stay on the device, owned by the handle, until hom_destroy or the next
+ * solve of the same order.  Returns HOM_ERR_NOT_CONVERGED if any load missed tol. */
+HOM_API hom_status hom_solve(hom_t h, int32_t order, int32_t n_loads, const double* loads,
+                             double tol, hom_solve_info* info);
+
+/* Effective tensors as FP64 voxel means of the stress of each load (host array out):
+ *  order 0: 6 x n_loads, column A = <C : (E^A + eps^A)> (the 6x6 C_eff for unit loads);
+ *  order 1: 6 x 18, column = <C : eps_2 + p_2> (mean order-2 stress of the paper's alpha=2);
+ *  order 2: 6 x 36, column = <C : eps_3 + p_3>. */
+HOM_API hom_status hom_effective(hom_t h, int32_t order, double* out);
+
+/* Copies one corrector field of a solved order to dst (double):
+ *  HOM_FIELD_STRAIN       6 x [N3][N2][N1] Mandel strain fluctuation eps;
+ *  HOM_FIELD_DISPLACEMENT 3 x [N3][N2][N1] zero-mean displacement u with e_y(u) = eps;
+ *  HOM_FIELD_STRESS       6 x [N3][N2][N1] Mandel stress (C : (E + eps) for order 0,
+ *                         C : eps + p for orders 1 and 2).
+ * dst is a device pointer if dst_on_device != 0, else a host pointer. */
+HOM_API hom_status hom_get_field(hom_t h, int32_t order, int32_t load, int32_t kind, double* dst,
+                                 int32_t dst_on_device);
+
+/* One Lippmann-Schwinger step on caller device buffers (Sec. 2, Algorithm 1 loop body):
+ *   eps_out = -Gamma0 * [(C - C0) : (eps_in + E)]
+ * eps_in, eps_out: device double [nrhs][6][N3][N2][N1] Mandel (eps_in NULL = zero field);
+ * E: host double [nrhs][6] Mandel (NULL = zero).  Computed in the handle's precision. */
+HOM_API hom_status hom_ls_apply(hom_t h, int32_t nrhs, const double* eps_in, const double* E,
+                                double* eps_out);
+
+/* Forward 3-D real-to-complex DFT, X[k] = sum_n x[n] exp(-2 pi i k.n/N) (unnormalised):
+ * f: device double [nfield][N3][N2][N1]; fhat: device double complex (interleaved re, im)
+ * [nfield][N3][N2][N1/2+1].  Computed in the handle's precision. */
+HOM_API hom_status hom_fft_forward(hom_t h, int32_t nfield, const double* f, double* fhat);
+
+/* Inverse of hom_fft_forward without the 1/M factor: f[n] = sum_k X[k] exp(+2 pi i k.n/N)
+ * over the Hermitian-completed spectrum.  fhat is not modified. */
+HOM_API hom_status hom_fft_inverse(hom_t h, int32_t nfield, const double* fhat, double* f);
+
+/* Green contraction at every frequency of the half spectrum (Sec. 2, Gamma0_hat formula):
+ *   eta_hat(xi) = -Gamma0_hat(xi) : tau_hat(xi),  eta_hat = 0 where xi = 0,
+ * tau_hat, eta_hat: device double complex [nrhs][6][N3][N2][N1/2+1] Mandel. */
+HOM_API hom_status hom_green_apply(hom_t h, int32_t nrhs, const double* tau_hat, double* eta_hat);
+
+/* Bytes of device memory the handle holds now. */
+HOM_API int64_t hom_device_bytes(hom_t h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+HOM_API const char* hom_last_error(hom_t h);
+
+/* Static name of a status code. */
+HOM_API const char* hom_status_string(hom_status s);
+
+/* Releases the handle and all device memory it holds (NULL is a no-op). */
+HOM_API void hom_destroy(hom_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOM_H */

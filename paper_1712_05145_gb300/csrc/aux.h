@@ -1,0 +1,25 @@
+// Pointwise / layout / reduction kernels used by the host driver (aux_kernels.cu).
+#pragma once
+#include "internal.h"
+
+namespace hom {
+
+template <typename Tf>
+cudaError_t launch_mandel_to_kelvin(const double* in, Tf* out, long long M, int nf, cudaStream_t s);
+template <typename Tf>
+cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int nf, cudaStream_t s);
+template <typename Ti, typename To>
+cudaError_t launch_convert(const Ti* in, To* out, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spec_from_std(const double* in, cx<T>* S, const Geo& g, int nf, int ncomp, int basis,
+                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_spec_to_std(const cx<T>* S, double* out, const Geo& g, int nf, int ncomp, int basis,
+                               cudaStream_t s);
+// out[rhs * ncomp + c] = mean over voxels of w(phase, c) * (f[rhs][c] + shift[rhs][c])
+template <typename Tf>
+cudaError_t launch_weighted_mean(const Tf* f, int ncomp, int nrhs, const double* shift, const uint8_t* phase,
+                                 const double* mat, int wsel, long long M, double* part, int nblk, double* out,
+                                 cudaStream_t s);
+
+}  // namespace hom

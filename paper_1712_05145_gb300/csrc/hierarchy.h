@@ -1,0 +1,25 @@
+// Pointwise kernels of the order-alpha problems (Sec. 3) and stress fields.
+#pragma once
+#include "internal.h"
+
+namespace hom {
+
+// Builds, for every load of order `order` (1 or 2), the polarization p_alpha (Kelvin,
+// components 0..5) and the body force g_alpha (Cartesian, components 6..8) into
+// out9 [nload][9][M], and copies p_alpha into pf [nload][6][M].
+//  order 1 (paper alpha = 2), load 3A+k:  p = C : sym(chi^A (x) e_k),  g = sigma^A e_k,
+//          sigma^A = C : (E^A + eps^A)   from the order-0 correctors (disp0, eps0, EK).
+//  order 2 (paper alpha = 3), load 6A+P, (k,l) the P-th Mandel pair, w = 1/(1+d_kl):
+//          p = C : w [sym(u^(A,k) (x) e_l) + sym(u^(A,l) (x) e_k)],
+//          g_i = w [s^(A,k)_il + s^(A,l)_ik],  s = C : eps_2 + p_2  from the order-1 correctors.
+template <typename Tf>
+cudaError_t launch_rhs_pointwise(int order, int nload, const Tf* disp, const Tf* eps, const Tf* pprev,
+                                 const double* EK, const uint8_t* phase, const double* mat, long long M,
+                                 Tf* out9, Tf* pf, cudaStream_t s);
+
+// Mandel stress of one load: C : (eps + E) (EK non-null) or C : eps + p (pf non-null).
+template <typename Tf>
+cudaError_t launch_stress_field(const Tf* eps, const double* EK, const Tf* pf, const uint8_t* phase,
+                                const double* mat, long long M, double* out, cudaStream_t s);
+
+}  // namespace hom

@@ -1,0 +1,1052 @@
+// Host driver and C ABI of libhom (see include/hom.h).
+//
+// A handle owns the RVE on the device (phase array, per-phase Kelvin eigenvalues of
+// C - C0 and C, twiddle tables), the spectrum scratch, the per-load solver state and the
+// correctors of every solved order.  Solvers run entirely on the device: the host only
+// launches kernels and reads back a few status words every `check_every` iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aux.h"
+#include "hierarchy.h"
+#include "hom.h"
+#include "internal.h"
+
+using namespace hom;
+
+namespace {
+
+const double kSqrt2 = 1.41421356237309504880;
+const double kR3 = 0.57735026918962576451, kR2 = 0.70710678118654752440, kR6 = 0.40824829046386301637;
+
+void mandel_to_kelvin6(const double* m, double* k) {
+  k[0] = (m[0] + m[1] + m[2]) * kR3;
+  k[1] = (m[0] - m[1]) * kR2;
+  k[2] = (m[0] + m[1] - 2.0 * m[2]) * kR6;
+  k[3] = m[3];
+  k[4] = m[4];
+  k[5] = m[5];
+}
+void kelvin_to_mandel6(const double* k, double* m) {
+  m[0] = k[0] * kR3 + k[1] * kR2 + k[2] * kR6;
+  m[1] = k[0] * kR3 - k[1] * kR2 + k[2] * kR6;
+  m[2] = k[0] * kR3 - 2.0 * k[2] * kR6;
+  m[3] = k[3];
+  m[4] = k[4];
+  m[5] = k[5];
+}
+
+}  // namespace
+
+struct OrderData {
+  bool solved = false;
+  int nloads = 0;
+  void* eps = nullptr;    // Tf [nloads][6][M] Kelvin strain fluctuation
+  void* disp = nullptr;   // Tf [nloads][3][M] displacement corrector
+  void* pf = nullptr;     // Tf [nloads][6][M] Kelvin polarization p_alpha (orders >= 1)
+  std::vector<double> loadsK;  // order 0: [nloads][6] Kelvin macroscopic strains
+  std::vector<double> eff;     // [6][nloads] Mandel mean stresses
+};
+
+struct hom_ctx {
+  Geo g{};
+  int nphase = 0;
+  double lam0 = 0, mu0 = 0;
+  hom_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  bool fp32 = true;
+  uint8_t* d_phase = nullptr;
+  double* d_mat64 = nullptr;
+  float* d_mat32 = nullptr;
+  cx<double>* d_tw64 = nullptr;
+  cx<float>* d_tw32 = nullptr;
+  long long tw_off[4] = {0, 0, 0, 0};
+  void* d_S = nullptr;  // compute-precision spectrum, `chunk` loads (>= 9 component planes)
+  size_t S_rhs_bytes = 0;
+  int chunk = 1;
+  int S_comps = 6;      // component planes d_S holds (per z-plane set)
+  cx<double>* d_S64 = nullptr;  // FP64 spectrum for residual sweeps (FP32 mode)
+  int chunk64 = 1;
+  int cap = 0;  // loads the state / partial arrays hold
+  RhsState* d_st = nullptr;
+  double* d_part = nullptr;  // [2][cap][2][6*n3]
+  unsigned* d_cnt = nullptr; // [2][cap]
+  double* d_E = nullptr;     // [cap][6]
+  double* d_mpart = nullptr; // mean reduction partials
+  double* d_mout = nullptr;
+  int mblk = 64;
+  void* d_work[3] = {nullptr, nullptr, nullptr};
+  size_t work_bytes[3] = {0, 0, 0};
+  OrderData ord[3];
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+hom_status fail(hom_ctx* c, hom_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(...)                                                                                \
+  do {                                                                                         \
+    cudaError_t e_ = (__VA_ARGS__);                                                            \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(c, HOM_ERR_CUDA, "%s failed: %s (%s:%d)", #__VA_ARGS__,                      \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                 \
+  } while (0)
+
+#define CKS(...)                         \
+  do {                                   \
+    hom_status s_ = (__VA_ARGS__);       \
+    if (s_ != HOM_OK) return s_;         \
+  } while (0)
+
+hom_status dalloc(hom_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, HOM_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->bytes += bytes;
+  c->allocs.push_back(*p);
+  return HOM_OK;
+}
+
+void dfree(hom_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  c->bytes -= bytes;
+  c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
+}
+
+size_t field_bytes(const hom_ctx* c, int nf, int ncomp) {
+  return (size_t)nf * ncomp * (size_t)c->g.M * (c->fp32 ? sizeof(float) : sizeof(double));
+}
+
+// grows work buffer i to at least `bytes`
+hom_status work(hom_ctx* c, int i, size_t bytes, void** out) {
+  if (c->work_bytes[i] < bytes) {
+    dfree(c, c->d_work[i], c->work_bytes[i]);
+    c->d_work[i] = nullptr;
+    c->work_bytes[i] = 0;
+    CKS(dalloc(c, &c->d_work[i], bytes));
+    c->work_bytes[i] = bytes;
+  }
+  *out = c->d_work[i];
+  return HOM_OK;
+}
+
+// grows the per-load state, partial and load arrays to `n` loads
+hom_status ensure_cap(hom_ctx* c, int n) {
+  if (n <= c->cap) return HOM_OK;
+  const size_t ncta = 6 * (size_t)c->g.n3 + 64;
+  if (c->d_st) {
+    dfree(c, c->d_st, sizeof(RhsState) * c->cap);
+    dfree(c, c->d_part, sizeof(double) * 2 * c->cap * 2 * ncta);
+    dfree(c, c->d_cnt, sizeof(unsigned) * 2 * c->cap);
+    dfree(c, c->d_E, sizeof(double) * 6 * c->cap);
+    dfree(c, c->d_mpart, sizeof(double) * (size_t)c->cap * 9 * c->mblk);
+    dfree(c, c->d_mout, sizeof(double) * (size_t)c->cap * 9);
+  }
+  c->cap = n;
+  CKS(dalloc(c, (void**)&c->d_st, sizeof(RhsState) * n));
+  CKS(dalloc(c, (void**)&c->d_part, sizeof(double) * 2 * n * 2 * ncta));
+  CKS(dalloc(c, (void**)&c->d_cnt, sizeof(unsigned) * 2 * n));
+  CKS(dalloc(c, (void**)&c->d_E, sizeof(double) * 6 * n));
+  CKS(dalloc(c, (void**)&c->d_mpart, sizeof(double) * (size_t)n * 9 * c->mblk));
+  CKS(dalloc(c, (void**)&c->d_mout, sizeof(double) * (size_t)n * 9));
+  CK(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned) * 2 * n, c->stream));
+  CK(cudaMemsetAsync(c->d_st, 0, sizeof(RhsState) * n, c->stream));
+  return HOM_OK;
+}
+
+double* part_fwd(hom_ctx* c) { return c->d_part; }
+double* part_inv(hom_ctx* c) { return c->d_part + (size_t)c->cap * 2 * (6 * (size_t)c->g.n3 + 64); }
+unsigned* cnt_fwd(hom_ctx* c) { return c->d_cnt; }
+unsigned* cnt_inv(hom_ctx* c) { return c->d_cnt + c->cap; }
+
+template <typename T> const T* mat_ptr(hom_ctx* c);
+template <> const float* mat_ptr<float>(hom_ctx* c) { return c->d_mat32; }
+template <> const double* mat_ptr<double>(hom_ctx* c) { return c->d_mat64; }
+template <typename T> const cx<T>* tw(hom_ctx* c, int i);
+template <> const cx<float>* tw<float>(hom_ctx* c, int i) { return c->d_tw32 + c->tw_off[i]; }
+template <> const cx<double>* tw<double>(hom_ctx* c, int i) { return c->d_tw64 + c->tw_off[i]; }
+
+template <typename Tf, typename T>
+FwdArgs<Tf, T> fwd_args(hom_ctx* c, int mode, int ncomp, int in_ncomp) {
+  FwdArgs<Tf, T> a{};
+  a.g = c->g;
+  a.mode = mode;
+  a.ncomp = ncomp;
+  a.in_ncomp = in_ncomp;
+  a.phase = c->d_phase;
+  a.mat = mat_ptr<T>(c);
+  a.n_phase = c->nphase;
+  a.part = part_fwd(c);
+  a.cnt = cnt_fwd(c);
+  a.tw_h = tw<T>(c, 0);
+  a.tw_n1 = tw<T>(c, 1);
+  a.tw_n2 = tw<T>(c, 2);
+  return a;
+}
+template <typename T>
+ZArgs<T> z_args(hom_ctx* c, int mode, int nin, int nout) {
+  ZArgs<T> a{};
+  a.g = c->g;
+  a.mode = mode;
+  a.ncomp_in = nin;
+  a.ncomp_out = nout;
+  a.lam0 = c->lam0;
+  a.mu0 = c->mu0;
+  a.scale = 1.0 / (double)c->g.M;
+  a.tw_n3 = tw<T>(c, 3);
+  zpass_tiling<T>(a);
+  return a;
+}
+template <typename Tf, typename T>
+InvArgs<Tf, T> inv_args(hom_ctx* c, int mode, int fin, int ncomp, int out_ncomp, int s_ncomp) {
+  InvArgs<Tf, T> a{};
+  a.g = c->g;
+  a.mode = mode;
+  a.fin = fin;
+  a.ncomp = ncomp;
+  a.out_ncomp = out_ncomp;
+  a.s_ncomp = s_ncomp;
+  a.c0h = (T)(3.0 * c->lam0 + 2.0 * c->mu0);
+  a.c0d = (T)(2.0 * c->mu0);
+  a.part = part_inv(c);
+  a.cnt = cnt_inv(c);
+  a.tw_h = tw<T>(c, 0);
+  a.tw_n1 = tw<T>(c, 1);
+  a.tw_n2 = tw<T>(c, 2);
+  return a;
+}
+
+template <typename T> cx<T>* spec(hom_ctx* c, int* chunk);
+template <> cx<float>* spec<float>(hom_ctx* c, int* chunk) {
+  *chunk = c->chunk;
+  return reinterpret_cast<cx<float>*>(c->d_S);
+}
+template <> cx<double>* spec<double>(hom_ctx* c, int* chunk) {
+  if (c->fp32) {
+    *chunk = c->chunk64;
+    return c->d_S64;
+  }
+  *chunk = c->chunk;
+  return reinterpret_cast<cx<double>*>(c->d_S);
+}
+
+// One full LS pass (plane_fwd, zpass, plane_inv) over loads [0, nrhs), chunk by chunk.
+template <typename Tf, typename T>
+hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf, T> fa, ZArgs<T> za, InvArgs<Tf, T> ia,
+                   const std::vector<int>* active = nullptr) {
+  int chunk;
+  cx<T>* S = spec<T>(c, &chunk);
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int n = std::min(chunk, nrhs - r0);
+    if (active) {
+      bool any = false;
+      for (int i = r0; i < r0 + n; ++i) any = any || (*active)[i];
+      if (!any) continue;
+    }
+    fa.rhs0 = za.rhs0 = ia.rhs0 = r0;
+    fa.S = S;
+    za.S = S;
+    ia.S = S;
+    CK(launch_plane_fwd<Tf, T>(fa, n, c->stream));
+    CK(launch_zpass<T>(za, n, c->stream));
+    CK(launch_plane_inv<Tf, T>(ia, n, c->stream));
+  }
+  return HOM_OK;
+}
+
+hom_status read_states(hom_ctx* c, int n, std::vector<RhsState>& h) {
+  h.resize(n);
+  CK(cudaMemcpyAsync(h.data(), c->d_st, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+hom_status write_states(hom_ctx* c, const std::vector<RhsState>& h) {
+  CK(cudaMemcpyAsync(c->d_st, h.data(), sizeof(RhsState) * h.size(), cudaMemcpyHostToDevice, c->stream));
+  return HOM_OK;
+}
+
+// Solves A x = b (Eq. cg_form) for n loads.  b = -Gamma0 * (C : E) for Kelvin loads dE
+// (order 0, dE device [n][6]) or b = bfield (higher orders).  x receives the solution.
+template <typename Tf, typename T>
+hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, Tf* x, double tol,
+                        hom_solve_info* info) {
+  using TR = double;  // residual sweeps always run the FFTs in FP64
+  CKS(ensure_cap(c, n));
+  const size_t fb = field_bytes(c, n, 6);
+  void *vr, *vp;
+  CKS(work(c, 0, fb, &vr));
+  CKS(work(c, 1, fb, &vp));
+  Tf* r = reinterpret_cast<Tf*>(vr);
+  Tf* p = reinterpret_cast<Tf*>(vp);
+  const bool basic = (c->opt.scheme == HOM_BASIC);
+  const double tol_inner = c->fp32 ? 0.5 * tol : tol;
+
+  std::vector<RhsState> st(n);
+  for (int i = 0; i < n; ++i) {
+    RhsState s{};
+    s.tol = tol_inner;
+    s.max_iter = c->opt.max_iter;
+    s.active = 1;
+    s.restart = 1;
+    st[i] = s;
+  }
+  CKS(write_states(c, st));
+  std::vector<int> refine(n, 0), done(n, 0);
+
+  if (basic) {
+    // eps_0 = b (Algorithm 1 INIT), then eps_{k+1} = b + T(eps_k) = T(eps_k + E) [+ b field]
+    Tf* buf[2] = {x, p};
+    {
+      auto fa = fwd_args<Tf, T>(c, FWD_TAU, 6, 6);
+      fa.E = dE;
+      fa.st = c->d_st;
+      auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+      za.st = c->d_st;
+      auto ia = inv_args<Tf, T>(c, INV_STORE, FIN_RHS, 6, 6, 6);
+      ia.out = buf[0];
+      ia.b = bfield;
+      ia.st = c->d_st;
+      CKS((ls_pass<Tf, T>(c, n, fa, za, ia)));
+    }
+    int it = 0;
+    std::vector<int> act(n, 1);
+    while (true) {
+      for (int k = 0; k < c->opt.check_every; ++k, ++it) {
+        auto fa = fwd_args<Tf, T>(c, FWD_TAU, 6, 6);
+        fa.in = buf[it & 1];
+        fa.E = dE;
+        fa.st = c->d_st;
+        auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+        za.st = c->d_st;
+        auto ia = inv_args<Tf, T>(c, INV_STORE, FIN_BASIC, 6, 6, 6);
+        ia.out = buf[(it + 1) & 1];
+        ia.prev = buf[it & 1];
+        ia.b = bfield;
+        ia.st = c->d_st;
+        CKS((ls_pass<Tf, T>(c, n, fa, za, ia, &act)));
+      }
+      CKS(read_states(c, n, st));
+      bool any = false;
+      for (int i = 0; i < n; ++i) {
+        act[i] = st[i].active;
+        any = any || st[i].active;
+      }
+      if (!any) break;
+    }
+    // the result of load i sits in buf[iter_i & 1]
+    for (int i = 0; i < n; ++i) {
+      if (st[i].iter & 1) {
+        const size_t one = field_bytes(c, 1, 6);
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(buf[0]) + one * i, reinterpret_cast<char*>(buf[1]) + one * i,
+                           one, cudaMemcpyDeviceToDevice, c->stream));
+      }
+    }
+  } else {
+    // r = b - A x with x = 0, in FP64 FFTs
+    CK(cudaMemsetAsync(x, 0, fb, c->stream));
+    {
+      auto fa = fwd_args<Tf, TR>(c, FWD_TAU, 6, 6);
+      fa.E = dE;
+      fa.st = c->d_st;
+      auto za = z_args<TR>(c, Z_GAMMA, 6, 6);
+      za.st = c->d_st;
+      auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RHS, 6, 6, 6);
+      ia.out = r;
+      ia.b = bfield;
+      ia.st = c->d_st;
+      CKS((ls_pass<Tf, TR>(c, n, fa, za, ia)));
+    }
+    CKS(read_states(c, n, st));
+    std::vector<int> act(n, 1);
+    for (int i = 0; i < n; ++i) {
+      if (st[i].b2 == 0.0) {  // b = 0: x = 0 is exact
+        done[i] = 1;
+        act[i] = 0;
+        st[i].active = 0;
+        st[i].res_true = 0.0;
+      }
+    }
+    CKS(write_states(c, st));
+    while (true) {
+      // inner CG
+      bool any = false;
+      for (int i = 0; i < n; ++i) any = any || act[i];
+      while (any) {
+        for (int k = 0; k < c->opt.check_every; ++k) {
+          auto fa = fwd_args<Tf, T>(c, FWD_CG, 6, 6);
+          fa.r = r;
+          fa.p = p;
+          fa.st = c->d_st;
+          auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+          za.st = c->d_st;
+          auto ia = inv_args<Tf, T>(c, INV_CG, FIN_CG, 6, 6, 6);
+          ia.p = p;
+          ia.x = x;
+          ia.r = r;
+          ia.st = c->d_st;
+          CKS((ls_pass<Tf, T>(c, n, fa, za, ia, &act)));
+        }
+        CKS(read_states(c, n, st));
+        any = false;
+        for (int i = 0; i < n; ++i) {
+          act[i] = st[i].active;
+          any = any || act[i];
+        }
+      }
+      // FP64 residual sweep r = b - A x for loads not yet finished
+      bool need = false;
+      for (int i = 0; i < n; ++i) {
+        const bool run = !done[i] && st[i].status == 0;
+        st[i].active = run ? 1 : 0;
+        act[i] = run;
+        need = need || run;
+      }
+      if (!need) break;
+      CKS(write_states(c, st));
+      {
+        auto fa = fwd_args<Tf, TR>(c, FWD_TAU, 6, 6);
+        fa.in = x;
+        fa.E = dE;
+        fa.st = c->d_st;
+        auto za = z_args<TR>(c, Z_GAMMA, 6, 6);
+        za.st = c->d_st;
+        auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RESID, 6, 6, 6);
+        ia.out = r;
+        ia.b = bfield;
+        ia.sub = x;
+        ia.st = c->d_st;
+        CKS((ls_pass<Tf, TR>(c, n, fa, za, ia, &act)));
+      }
+      CKS(read_states(c, n, st));
+      bool again = false;
+      for (int i = 0; i < n; ++i) {
+        if (!act[i]) continue;
+        if (st[i].res_true < tol) {
+          done[i] = 1;
+          st[i].active = 0;
+        } else if (refine[i] < c->opt.max_refine && st[i].iter < st[i].max_iter) {
+          refine[i] += 1;
+          st[i].active = 1;  // restart CG from the FP64 residual
+          again = true;
+        } else {
+          st[i].active = 0;
+          st[i].status = 1;
+        }
+        act[i] = st[i].active;
+      }
+      CKS(write_states(c, st));
+      if (!again) break;
+    }
+  }
+
+  if (basic) {
+    // report the FP64 residual of the fixed point
+    std::vector<int> act(n, 1);
+    for (int i = 0; i < n; ++i) st[i].active = 1;
+    CKS(write_states(c, st));
+    auto fa = fwd_args<Tf, TR>(c, FWD_TAU, 6, 6);
+    fa.in = x;
+    fa.E = dE;
+    fa.st = c->d_st;
+    auto za = z_args<TR>(c, Z_GAMMA, 6, 6);
+    za.st = c->d_st;
+    auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RESID, 6, 6, 6);
+    ia.out = r;
+    ia.b = bfield;
+    ia.sub = x;
+    ia.st = c->d_st;
+    // FIN_RESID overwrites res; keep the Cauchy quantity for the report
+    std::vector<RhsState> before = st;
+    CKS((ls_pass<Tf, TR>(c, n, fa, za, ia, &act)));
+    CKS(read_states(c, n, st));
+    for (int i = 0; i < n; ++i) {
+      st[i].res = before[i].res;
+      st[i].status = before[i].status;
+    }
+  }
+
+  hom_status worst = HOM_OK;
+  for (int i = 0; i < n; ++i) {
+    hom_status si = HOM_OK;
+    if (st[i].status == 2) si = HOM_ERR_NUMERIC;
+    else if (st[i].status == 1 || (!basic && !done[i]) || (basic && st[i].res_true >= tol && st[i].res >= tol))
+      si = HOM_ERR_NOT_CONVERGED;
+    if (info) {
+      info[i].iterations = st[i].iter;
+      info[i].refinements = refine[i];
+      info[i].status = si;
+      info[i].reserved = 0;
+      info[i].rel_residual = st[i].res;
+      info[i].rel_residual_fp64 = st[i].res_true;
+    }
+    if (si == HOM_ERR_NUMERIC) worst = si;
+    else if (si != HOM_OK && worst == HOM_OK) worst = si;
+  }
+  if (worst == HOM_ERR_NOT_CONVERGED) fail(c, worst, "at least one load did not reach the tolerance");
+  if (worst == HOM_ERR_NUMERIC) fail(c, worst, "NaN or Inf in a reduction");
+  return worst;
+}
+
+hom_status alloc_order(hom_ctx* c, int order, int nloads, bool with_p) {
+  OrderData& o = c->ord[order];
+  if (o.eps && o.nloads == nloads) return HOM_OK;
+  if (o.eps) dfree(c, o.eps, field_bytes(c, o.nloads, 6));
+  if (o.disp) dfree(c, o.disp, field_bytes(c, o.nloads, 3));
+  if (o.pf) dfree(c, o.pf, field_bytes(c, o.nloads, 6));
+  o.eps = o.disp = o.pf = nullptr;
+  o.nloads = nloads;
+  CKS(dalloc(c, &o.eps, field_bytes(c, nloads, 6)));
+  CKS(dalloc(c, &o.disp, field_bytes(c, nloads, 3)));
+  if (with_p) CKS(dalloc(c, &o.pf, field_bytes(c, nloads, 6)));
+  return HOM_OK;
+}
+
+// mean stress <C : (eps + E)> (order 0) or <C : eps + p> (higher orders), Mandel [6][n]
+template <typename Tf>
+hom_status mean_stress(hom_ctx* c, int order, std::vector<double>& eff) {
+  OrderData& o = c->ord[order];
+  const int n = o.nloads;
+  CKS(ensure_cap(c, n));
+  std::vector<double> hk(n * 6), hp(n * 6, 0.0);
+  if (order == 0) CK(cudaMemcpyAsync(c->d_E, o.loadsK.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice,
+                                     c->stream));
+  CK(launch_weighted_mean<Tf>(reinterpret_cast<const Tf*>(o.eps), 6, n, order == 0 ? c->d_E : nullptr,
+                              c->d_phase, c->d_mat64, 2, c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
+  CK(cudaMemcpyAsync(hk.data(), c->d_mout, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (order > 0) {
+    CK(launch_weighted_mean<Tf>(reinterpret_cast<const Tf*>(o.pf), 6, n, nullptr, c->d_phase, c->d_mat64, -1,
+                                c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
+    CK(cudaMemcpyAsync(hp.data(), c->d_mout, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  eff.assign(6 * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double k[6], m[6];
+    for (int i = 0; i < 6; ++i) k[i] = hk[j * 6 + i] + hp[j * 6 + i];
+    kelvin_to_mandel6(k, m);
+    for (int i = 0; i < 6; ++i) eff[i * n + j] = m[i];
+  }
+  return HOM_OK;
+}
+
+// Displacement correctors u (e_y(u) = eps, zero mean) of every load of `order`:
+// forward FFT of the strain, u_hat = -i (2 eps_hat xi - xi (xi . eps_hat xi)/|xi|^2)/|xi|^2,
+// inverse FFT of the 3 components.
+template <typename Tf>
+hom_status displacements(hom_ctx* c, int order) {
+  OrderData& o = c->ord[order];
+  const int n = o.nloads;
+  int chunk;
+  cx<Tf>* S = spec<Tf>(c, &chunk);
+  chunk = c->S_comps / 6;
+  for (int r0 = 0; r0 < n; r0 += chunk) {
+    const int m = std::min(chunk, n - r0);
+    auto fa = fwd_args<Tf, Tf>(c, FWD_COPY, 6, 6);
+    fa.in = reinterpret_cast<const Tf*>(o.eps);
+    fa.rhs0 = r0;
+    fa.S = S;
+    CK((launch_plane_fwd<Tf, Tf>(fa, m, c->stream)));
+    auto za = z_args<Tf>(c, Z_DISP, 6, 3);
+    za.S = S;
+    za.rhs0 = r0;
+    CK(launch_zpass<Tf>(za, m, c->stream));
+    auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 3, 3, 6);
+    ia.S = S;
+    ia.rhs0 = r0;
+    ia.out = reinterpret_cast<Tf*>(o.disp);
+    CK((launch_plane_inv<Tf, Tf>(ia, m, c->stream)));
+  }
+  return HOM_OK;
+}
+
+// Right-hand sides b = -Gamma0 * (p_alpha + theta_alpha) of order 1 or 2 (Sec. 3, modified
+// initialization), with p_alpha kept in pf for the effective tensor.
+template <typename Tf>
+hom_status build_rhs(hom_ctx* c, int order, Tf* b, Tf* pf) {
+  const int n = (order == 1) ? 18 : 36;
+  const OrderData& lo = c->ord[order - 1];
+  void* v9;
+  CKS(work(c, 0, field_bytes(c, n, 9), &v9));
+  Tf* f9 = reinterpret_cast<Tf*>(v9);
+  CKS(ensure_cap(c, std::max(n, 6)));
+  if (order == 1)
+    CK(cudaMemcpyAsync(c->d_E, c->ord[0].loadsK.data(), sizeof(double) * 36, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_rhs_pointwise<Tf>(order, n, reinterpret_cast<const Tf*>(lo.disp), reinterpret_cast<const Tf*>(lo.eps),
+                              order == 2 ? reinterpret_cast<const Tf*>(lo.pf) : nullptr, c->d_E, c->d_phase,
+                              c->d_mat64, c->g.M, f9, pf, c->stream));
+  int chunk;
+  cx<Tf>* S = spec<Tf>(c, &chunk);
+  chunk = std::max(1, c->S_comps / 9);
+  for (int r0 = 0; r0 < n; r0 += chunk) {
+    const int m = std::min(chunk, n - r0);
+    auto fa = fwd_args<Tf, Tf>(c, FWD_COPY, 9, 9);
+    fa.in = f9;
+    fa.rhs0 = r0;
+    fa.S = S;
+    CK((launch_plane_fwd<Tf, Tf>(fa, m, c->stream)));
+    auto za = z_args<Tf>(c, Z_RHS, 9, 6);
+    za.S = S;
+    za.rhs0 = r0;
+    CK(launch_zpass<Tf>(za, m, c->stream));
+    auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 6, 6, 9);
+    ia.S = S;
+    ia.rhs0 = r0;
+    ia.out = b;
+    CK((launch_plane_inv<Tf, Tf>(ia, m, c->stream)));
+  }
+  return HOM_OK;
+}
+
+template <typename Tf>
+hom_status export_field(hom_ctx* c, int order, int load, int kind, double* d) {
+  const OrderData& o = c->ord[order];
+  const long long M = c->g.M;
+  if (kind == HOM_FIELD_STRAIN) {
+    CK(launch_kelvin_to_mandel<Tf>(reinterpret_cast<const Tf*>(o.eps) + (long long)load * 6 * M, d, M, 1,
+                                   c->stream));
+  } else if (kind == HOM_FIELD_DISPLACEMENT) {
+    CK((launch_convert<Tf, double>(reinterpret_cast<const Tf*>(o.disp) + (long long)load * 3 * M, d, 3 * M,
+                                   c->stream)));
+  } else {
+    const double* ek = nullptr;
+    if (order == 0) {
+      CK(cudaMemcpyAsync(c->d_E, &o.loadsK[load * 6], sizeof(double) * 6, cudaMemcpyHostToDevice, c->stream));
+      ek = c->d_E;
+    }
+    CK(launch_stress_field<Tf>(reinterpret_cast<const Tf*>(o.eps) + (long long)load * 6 * M, ek,
+                               order > 0 ? reinterpret_cast<const Tf*>(o.pf) + (long long)load * 6 * M : nullptr,
+                               c->d_phase, c->d_mat64, M, d, c->stream));
+  }
+  return HOM_OK;
+}
+
+template <typename Tf>
+hom_status solve_order0(hom_ctx* c, int n, const double* loads, double tol, hom_solve_info* info) {
+  CKS(alloc_order(c, 0, n, false));
+  OrderData& o = c->ord[0];
+  o.solved = false;
+  o.loadsK.assign(6 * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    if (loads) for (int j = 0; j < 6; ++j) m[j] = loads[i * 6 + j];
+    else m[i] = 1.0;
+    mandel_to_kelvin6(m, &o.loadsK[i * 6]);
+  }
+  CKS(ensure_cap(c, n));
+  CK(cudaMemcpyAsync(c->d_E, o.loadsK.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice, c->stream));
+  hom_status s = solve_system<Tf, Tf>(c, n, c->d_E, nullptr, reinterpret_cast<Tf*>(o.eps), tol, info);
+  if (s != HOM_OK && s != HOM_ERR_NOT_CONVERGED) return s;
+  CKS(mean_stress<Tf>(c, 0, o.eff));
+  hom_status sd = displacements<Tf>(c, 0);
+  if (sd != HOM_OK) return sd;
+  o.solved = (s == HOM_OK);
+  return s;
+}
+
+template <typename Tf>
+hom_status solve_higher(hom_ctx* c, int order, double tol, hom_solve_info* info) {
+  const int n = (order == 1) ? 18 : 36;
+  if (!c->ord[order - 1].solved || (order == 1 && c->ord[0].nloads != 6))
+    return fail(c, HOM_ERR_ORDER, "order %d needs a converged order %d with unit loads", order, order - 1);
+  CKS(alloc_order(c, order, n, true));
+  OrderData& o = c->ord[order];
+  o.solved = false;
+  void* vb;
+  CKS(work(c, 2, field_bytes(c, n, 6), &vb));
+  Tf* b = reinterpret_cast<Tf*>(vb);
+  CKS(build_rhs<Tf>(c, order, b, reinterpret_cast<Tf*>(o.pf)));
+  hom_status s = solve_system<Tf, Tf>(c, n, nullptr, b, reinterpret_cast<Tf*>(o.eps), tol, info);
+  if (s != HOM_OK && s != HOM_ERR_NOT_CONVERGED) return s;
+  CKS(mean_stress<Tf>(c, order, o.eff));
+  CKS(displacements<Tf>(c, order));
+  o.solved = (s == HOM_OK);
+  return s;
+}
+
+void twiddles(int n, std::vector<cx<double>>& out) {
+  for (int t = 0; t < n; ++t) {
+    const double a = -2.0 * M_PI * (double)t / (double)n;
+    cx<double> w;
+    w.re = std::cos(a);
+    w.im = std::sin(a);
+    out.push_back(w);
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+HOM_API void hom_default_options(hom_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = HOM_FP32_REFINE;
+  opt->scheme = HOM_CG;
+  opt->max_iter = 2000;
+  opt->check_every = 8;
+  opt->max_refine = 6;
+  opt->rhs_chunk = 0;
+  opt->l2_budget_bytes = 64LL << 20;
+  opt->cuda_stream = nullptr;
+}
+
+HOM_API const char* hom_status_string(hom_status s) {
+  switch (s) {
+    case HOM_OK: return "HOM_OK";
+    case HOM_ERR_ARG: return "HOM_ERR_ARG";
+    case HOM_ERR_SIZE: return "HOM_ERR_SIZE";
+    case HOM_ERR_NOMEM: return "HOM_ERR_NOMEM";
+    case HOM_ERR_NOT_CONVERGED: return "HOM_ERR_NOT_CONVERGED";
+    case HOM_ERR_ORDER: return "HOM_ERR_ORDER";
+    case HOM_ERR_NUMERIC: return "HOM_ERR_NUMERIC";
+    case HOM_ERR_TIMEOUT: return "HOM_ERR_TIMEOUT";
+    case HOM_ERR_CUDA: return "HOM_ERR_CUDA";
+  }
+  return "HOM_ERR_UNKNOWN";
+}
+
+HOM_API const char* hom_last_error(hom_t h) { return h ? h->err.c_str() : "null handle"; }
+
+HOM_API int64_t hom_device_bytes(hom_t h) { return h ? (int64_t)h->bytes : 0; }
+
+HOM_API void hom_destroy(hom_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32_t n_phase, const double* lame,
+                              double lambda0, double mu0, const hom_options* opt, hom_t* out) {
+  hom_ctx* c = nullptr;
+  if (!grid || !phase || !lame || !out) return HOM_ERR_ARG;
+  if (n_phase < 1 || n_phase > 256) return HOM_ERR_ARG;
+  if (!(mu0 != 0.0) || !(lambda0 + 2.0 * mu0 != 0.0) || !std::isfinite(lambda0) || !std::isfinite(mu0))
+    return HOM_ERR_ARG;
+  const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
+  if (n1 < 4 || (n1 & 1) || !fft_length_supported(n1 / 2) || !fft_length_supported(n2) ||
+      !fft_length_supported(n3))
+    return HOM_ERR_SIZE;
+  if ((long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
+
+  c = new hom_ctx();
+  hom_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  if (c->opt.max_iter < 1) c->opt.max_iter = 1;
+  if (c->opt.check_every < 1) c->opt.check_every = 1;
+  if (c->opt.max_refine < 0) c->opt.max_refine = 0;
+  if (c->opt.l2_budget_bytes <= 0) c->opt.l2_budget_bytes = 64LL << 20;
+  if (c->opt.precision != HOM_FP64 && c->opt.precision != HOM_FP32_REFINE) { delete c; return HOM_ERR_ARG; }
+  if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG) { delete c; return HOM_ERR_ARG; }
+  c->fp32 = (c->opt.precision == HOM_FP32_REFINE);
+  c->nphase = n_phase;
+  c->lam0 = lambda0;
+  c->mu0 = mu0;
+  cudaGetDevice(&c->device);
+  if (c->opt.cuda_stream) {
+    c->stream = reinterpret_cast<cudaStream_t>(c->opt.cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return HOM_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+
+  Geo& g = c->g;
+  g.n1 = n1;
+  g.n2 = n2;
+  g.n3 = n3;
+  g.h = n1 / 2;
+  g.P = (g.h & 1) ? g.h : g.h + 1;
+  g.M = (long long)n1 * n2 * n3;
+  g.plane_c = (long long)n2 * (g.h + 1);
+  {
+    const long long e = (long long)n2 * g.h;
+    int thr = (int)((e + 15) / 16);
+    thr = ((thr + 31) / 32) * 32;
+    g.thr_plane = std::max(128, std::min(512, thr));
+  }
+  const int nmax = std::max(n1, std::max(n2, n3));
+  g.xs1 = 2.0 * M_PI * nmax / n1;
+  g.xs2 = 2.0 * M_PI * nmax / n2;
+  g.xs3 = 2.0 * M_PI * nmax / n3;
+
+  auto bail = [&](hom_status s) {
+    hom_destroy(c);
+    return s;
+  };
+
+  // phase array (host or device source) and its range check
+  hom_status s;
+  if ((s = dalloc(c, (void**)&c->d_phase, (size_t)g.M)) != HOM_OK) return bail(s);
+  std::vector<uint8_t> hph((size_t)g.M);
+  if (is_device_ptr(phase)) {
+    if (cudaMemcpy(hph.data(), phase, (size_t)g.M, cudaMemcpyDeviceToHost) != cudaSuccess) return bail(HOM_ERR_CUDA);
+  } else {
+    std::memcpy(hph.data(), phase, (size_t)g.M);
+  }
+  for (size_t i = 0; i < hph.size(); ++i)
+    if (hph[i] >= n_phase) return bail(HOM_ERR_ARG);
+  if (cudaMemcpy(c->d_phase, hph.data(), (size_t)g.M, cudaMemcpyHostToDevice) != cudaSuccess) return bail(HOM_ERR_CUDA);
+
+  // per-phase Kelvin eigenvalues: C - C0 (3 dK, 2 dmu), C (3K, 2mu)
+  std::vector<double> m64(4 * 256, 0.0);
+  std::vector<float> m32(4 * 256, 0.0f);
+  for (int i = 0; i < n_phase; ++i) {
+    const double l = lame[2 * i], m = lame[2 * i + 1];
+    if (!std::isfinite(l) || !std::isfinite(m)) return bail(HOM_ERR_ARG);
+    m64[4 * i + 0] = 3.0 * (l - lambda0) + 2.0 * (m - mu0);
+    m64[4 * i + 1] = 2.0 * (m - mu0);
+    m64[4 * i + 2] = 3.0 * l + 2.0 * m;
+    m64[4 * i + 3] = 2.0 * m;
+    for (int j = 0; j < 4; ++j) m32[4 * i + j] = (float)m64[4 * i + j];
+  }
+  if ((s = dalloc(c, (void**)&c->d_mat64, sizeof(double) * 4 * 256)) != HOM_OK) return bail(s);
+  if ((s = dalloc(c, (void**)&c->d_mat32, sizeof(float) * 4 * 256)) != HOM_OK) return bail(s);
+  cudaMemcpy(c->d_mat64, m64.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_mat32, m32.data(), sizeof(float) * 4 * 256, cudaMemcpyHostToDevice);
+
+  // twiddle tables exp(-2 pi i t / L) for L = h, n1, n2, n3 (host libm, FP64)
+  std::vector<cx<double>> t64;
+  const int lens[4] = {g.h, n1, n2, n3};
+  for (int i = 0; i < 4; ++i) {
+    c->tw_off[i] = (long long)t64.size();
+    twiddles(lens[i], t64);
+  }
+  std::vector<cx<float>> t32(t64.size());
+  for (size_t i = 0; i < t64.size(); ++i) {
+    t32[i].re = (float)t64[i].re;
+    t32[i].im = (float)t64[i].im;
+  }
+  if ((s = dalloc(c, (void**)&c->d_tw64, sizeof(cx<double>) * t64.size())) != HOM_OK) return bail(s);
+  if ((s = dalloc(c, (void**)&c->d_tw32, sizeof(cx<float>) * t32.size())) != HOM_OK) return bail(s);
+  cudaMemcpy(c->d_tw64, t64.data(), sizeof(cx<double>) * t64.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(c->d_tw32, t32.data(), sizeof(cx<float>) * t32.size(), cudaMemcpyHostToDevice);
+
+  // spectrum scratch
+  const size_t elem = c->fp32 ? sizeof(cx<float>) : sizeof(cx<double>);
+  c->S_rhs_bytes = (size_t)6 * n3 * (size_t)g.plane_c * elem;
+  const size_t budget = (size_t)c->opt.l2_budget_bytes;
+  c->chunk = c->opt.rhs_chunk > 0 ? c->opt.rhs_chunk : (int)std::max<size_t>(1, budget / c->S_rhs_bytes);
+  c->chunk = std::min(c->chunk, 64);
+  c->S_comps = std::max(6 * c->chunk, 9);
+  if ((s = dalloc(c, &c->d_S, c->S_rhs_bytes / 6 * c->S_comps)) != HOM_OK) return bail(s);
+  if (c->fp32) {
+    const size_t b64 = (size_t)6 * n3 * (size_t)g.plane_c * sizeof(cx<double>);
+    c->chunk64 = (int)std::max<size_t>(1, budget / b64);
+    c->chunk64 = std::min(c->chunk64, 64);
+    if ((s = dalloc(c, (void**)&c->d_S64, b64 * c->chunk64)) != HOM_OK) return bail(s);
+  }
+  if ((s = ensure_cap(c, 6)) != HOM_OK) return bail(s);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
+  *out = c;
+  return HOM_OK;
+}
+
+HOM_API hom_status hom_solve(hom_t c, int32_t order, int32_t n_loads, const double* loads, double tol,
+                             hom_solve_info* info) {
+  if (!c) return HOM_ERR_ARG;
+  if (!(tol > 0.0)) return fail(c, HOM_ERR_ARG, "tol must be > 0");
+  if (order < 0 || order > 2) return fail(c, HOM_ERR_ARG, "order must be 0, 1 or 2");
+  if (order == 0) {
+    int n = loads ? n_loads : 6;
+    if (n < 1 || n > 64) return fail(c, HOM_ERR_ARG, "n_loads must be in 1..64");
+    for (int k = order + 1; k < 3; ++k) c->ord[k].solved = false;
+    return c->fp32 ? solve_order0<float>(c, n, loads, tol, info) : solve_order0<double>(c, n, loads, tol, info);
+  }
+  if (loads) return fail(c, HOM_ERR_ARG, "orders 1 and 2 take only the unit loads (loads = NULL)");
+  if (order == 1) {
+    const std::vector<double>& L = c->ord[0].loadsK;
+    bool unit = c->ord[0].nloads == 6;
+    if (unit) {
+      for (int i = 0; i < 6 && unit; ++i) {
+        double m[6];
+        kelvin_to_mandel6(&L[i * 6], m);
+        for (int j = 0; j < 6; ++j) unit = unit && std::fabs(m[j] - (i == j ? 1.0 : 0.0)) < 1e-14;
+      }
+    }
+    if (!unit || !c->ord[0].solved) return fail(c, HOM_ERR_ORDER, "order 1 needs order 0 solved for the unit loads");
+  }
+  if (order == 2 && !c->ord[1].solved) return fail(c, HOM_ERR_ORDER, "order 2 needs order 1 solved");
+  c->ord[order].solved = false;
+  if (order == 1) c->ord[2].solved = false;
+  return c->fp32 ? solve_higher<float>(c, order, tol, info) : solve_higher<double>(c, order, tol, info);
+}
+
+HOM_API hom_status hom_effective(hom_t c, int32_t order, double* out) {
+  if (!c || !out) return HOM_ERR_ARG;
+  if (order < 0 || order > 2) return fail(c, HOM_ERR_ARG, "order must be 0, 1 or 2");
+  const OrderData& o = c->ord[order];
+  if (o.eff.empty()) return fail(c, HOM_ERR_ORDER, "order %d has not been solved", order);
+  std::memcpy(out, o.eff.data(), sizeof(double) * o.eff.size());
+  return HOM_OK;
+}
+
+HOM_API hom_status hom_get_field(hom_t c, int32_t order, int32_t load, int32_t kind, double* dst,
+                                 int32_t dst_on_device) {
+  if (!c || !dst) return HOM_ERR_ARG;
+  if (order < 0 || order > 2) return fail(c, HOM_ERR_ARG, "order must be 0, 1 or 2");
+  const OrderData& o = c->ord[order];
+  if (!o.eps || o.eff.empty()) return fail(c, HOM_ERR_ORDER, "order %d has not been solved", order);
+  if (load < 0 || load >= o.nloads) return fail(c, HOM_ERR_ARG, "load out of range");
+  if (kind != HOM_FIELD_STRAIN && kind != HOM_FIELD_DISPLACEMENT && kind != HOM_FIELD_STRESS)
+    return fail(c, HOM_ERR_ARG, "unknown field kind");
+  const int nc = (kind == HOM_FIELD_DISPLACEMENT) ? 3 : 6;
+  const size_t nbytes = sizeof(double) * nc * (size_t)c->g.M;
+  double* d = dst;
+  void* tmp = nullptr;
+  if (!dst_on_device) {
+    CKS(work(c, 2, std::max(nbytes, c->work_bytes[2]), &tmp));
+    d = reinterpret_cast<double*>(tmp);
+  }
+  hom_status s = c->fp32 ? export_field<float>(c, order, load, kind, d) : export_field<double>(c, order, load, kind, d);
+  if (s != HOM_OK) return s;
+  if (!dst_on_device) CK(cudaMemcpyAsync(dst, d, nbytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+HOM_API hom_status hom_ls_apply(hom_t c, int32_t nrhs, const double* eps_in, const double* E, double* eps_out) {
+  if (!c || !eps_out || nrhs < 1 || nrhs > 64) return HOM_ERR_ARG;
+  CKS(ensure_cap(c, nrhs));
+  std::vector<double> ek(6 * nrhs, 0.0);
+  if (E) for (int i = 0; i < nrhs; ++i) mandel_to_kelvin6(E + 6 * i, &ek[6 * i]);
+  CK(cudaMemcpyAsync(c->d_E, ek.data(), sizeof(double) * 6 * nrhs, cudaMemcpyHostToDevice, c->stream));
+  void *vin = nullptr, *vout;
+  const size_t fb = field_bytes(c, nrhs, 6);
+  CKS(work(c, 1, fb, &vout));
+  if (eps_in) CKS(work(c, 0, fb, &vin));
+  if (c->fp32) {
+    if (eps_in) CK(launch_mandel_to_kelvin<float>(eps_in, (float*)vin, c->g.M, nrhs, c->stream));
+    auto fa = fwd_args<float, float>(c, FWD_TAU, 6, 6);
+    fa.in = (const float*)vin;
+    fa.E = c->d_E;
+    auto za = z_args<float>(c, Z_GAMMA, 6, 6);
+    auto ia = inv_args<float, float>(c, INV_STORE, FIN_NONE, 6, 6, 6);
+    ia.out = (float*)vout;
+    CKS((ls_pass<float, float>(c, nrhs, fa, za, ia)));
+    CK(launch_kelvin_to_mandel<float>((const float*)vout, eps_out, c->g.M, nrhs, c->stream));
+  } else {
+    if (eps_in) CK(launch_mandel_to_kelvin<double>(eps_in, (double*)vin, c->g.M, nrhs, c->stream));
+    auto fa = fwd_args<double, double>(c, FWD_TAU, 6, 6);
+    fa.in = (const double*)vin;
+    fa.E = c->d_E;
+    auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+    auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 6, 6, 6);
+    ia.out = (double*)vout;
+    CKS((ls_pass<double, double>(c, nrhs, fa, za, ia)));
+    CK(launch_kelvin_to_mandel<double>((const double*)vout, eps_out, c->g.M, nrhs, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+hom_status fft_fwd_impl(hom_ctx* c, int nf, const double* f, double* fhat) {
+  void *vin, *vs;
+  CKS(work(c, 0, sizeof(T) * (size_t)nf * c->g.M, &vin));
+  const size_t sb = sizeof(cx<T>) * (size_t)nf * c->g.n3 * c->g.plane_c;
+  CKS(work(c, 2, sb, &vs));
+  CK((launch_convert<double, T>(f, (T*)vin, (long long)nf * c->g.M, c->stream)));
+  auto fa = fwd_args<T, T>(c, FWD_COPY, nf, nf);
+  fa.in = (const T*)vin;
+  fa.S = (cx<T>*)vs;
+  CK((launch_plane_fwd<T, T>(fa, 1, c->stream)));
+  auto za = z_args<T>(c, Z_FWD, nf, nf);
+  za.S = (cx<T>*)vs;
+  CK(launch_zpass<T>(za, 1, c->stream));
+  CK(launch_spec_to_std<T>((const cx<T>*)vs, fhat, c->g, 1, nf, 0, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+template <typename T>
+hom_status fft_inv_impl(hom_ctx* c, int nf, const double* fhat, double* f) {
+  void *vout, *vs;
+  CKS(work(c, 0, sizeof(T) * (size_t)nf * c->g.M, &vout));
+  const size_t sb = sizeof(cx<T>) * (size_t)nf * c->g.n3 * c->g.plane_c;
+  CKS(work(c, 2, sb, &vs));
+  CK(launch_spec_from_std<T>(fhat, (cx<T>*)vs, c->g, 1, nf, 0, c->stream));
+  auto za = z_args<T>(c, Z_INV, nf, nf);
+  za.S = (cx<T>*)vs;
+  CK(launch_zpass<T>(za, 1, c->stream));
+  auto ia = inv_args<T, T>(c, INV_STORE, FIN_NONE, nf, nf, nf);
+  ia.S = (const cx<T>*)vs;
+  ia.out = (T*)vout;
+  CK((launch_plane_inv<T, T>(ia, 1, c->stream)));
+  CK((launch_convert<T, double>((const T*)vout, f, (long long)nf * c->g.M, c->stream)));
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+template <typename T>
+hom_status green_impl(hom_ctx* c, int nrhs, const double* th, double* eh) {
+  void* vs;
+  const size_t sb = sizeof(cx<T>) * (size_t)nrhs * 6 * c->g.n3 * c->g.plane_c;
+  CKS(work(c, 2, sb, &vs));
+  CK(launch_spec_from_std<T>(th, (cx<T>*)vs, c->g, nrhs, 6, 1, c->stream));
+  auto za = z_args<T>(c, Z_GREEN, 6, 6);
+  za.S = (cx<T>*)vs;
+  za.scale = 1.0;
+  CK(launch_zpass<T>(za, nrhs, c->stream));
+  CK(launch_spec_to_std<T>((const cx<T>*)vs, eh, c->g, nrhs, 6, 2, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+HOM_API hom_status hom_fft_forward(hom_t c, int32_t nfield, const double* f, double* fhat) {
+  if (!c || !f || !fhat || nfield < 1 || nfield > 64 || (long long)nfield * c->g.n3 > 8192) return HOM_ERR_ARG;
+  return c->fp32 ? fft_fwd_impl<float>(c, nfield, f, fhat) : fft_fwd_impl<double>(c, nfield, f, fhat);
+}
+HOM_API hom_status hom_fft_inverse(hom_t c, int32_t nfield, const double* fhat, double* f) {
+  if (!c || !f || !fhat || nfield < 1 || nfield > 64 || (long long)nfield * c->g.n3 > 8192) return HOM_ERR_ARG;
+  return c->fp32 ? fft_inv_impl<float>(c, nfield, fhat, f) : fft_inv_impl<double>(c, nfield, fhat, f);
+}
+HOM_API hom_status hom_green_apply(hom_t c, int32_t nrhs, const double* tau_hat, double* eta_hat) {
+  if (!c || !tau_hat || !eta_hat || nrhs < 1 || nrhs > 64) return HOM_ERR_ARG;
+  return c->fp32 ? green_impl<float>(c, nrhs, tau_hat, eta_hat) : green_impl<double>(c, nrhs, tau_hat, eta_hat);
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal (C++) interface between the host driver and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace hom {
+
+// Geometry of one voxel grid and its spectrum layout.
+//  fields   [rhs][comp][n3][n2][n1]            real, x fastest
+//  spectrum [rhs][comp][n3][plane_c]           complex; one x-y plane holds the
+//           n2 x h half-spectrum rows (kx < n1/2, row pitch h) followed by the
+//           n2 values of the Nyquist column kx = n1/2.
+struct Geo {
+  int n1, n2, n3, h;     // h = n1 / 2 (n1 even)
+  int P;                 // shared-memory row pitch of a plane (complex elements, odd)
+  long long M;           // voxels
+  long long plane_c;     // n2 * (h + 1)
+  int thr_plane;         // threads per CTA of the plane kernels
+  double xs1, xs2, xs3;  // physical frequency per integer wave number: 2 pi Nmax / N_i
+};
+
+// Per right-hand-side solver state, kept on the device (FP64).
+struct RhsState {
+  double rho;        // <r, r>_C0
+  double alpha, beta;
+  double pAp;        // <p, A p>_C0 = <p, C p>
+  double b2;         // ||b||^2 (voxel mean)
+  double res;        // latest relative residual (recursive / Cauchy)
+  double res_true;   // FP64 residual ||b - A x|| / ||b||
+  double tol;        // inner stopping tolerance
+  int iter;          // iterations done
+  int max_iter;
+  int active;        // 1 while the inner iteration runs
+  int restart;       // 1: next CG step starts from p = r
+  int status;        // 0 ok, 1 not converged, 2 numeric
+  int pad_;
+};
+
+enum FwdMode { FWD_TAU = 0, FWD_CG = 1, FWD_COPY = 2 };
+// Z_GAMMA: forward z FFT, -Gamma0_hat contraction, inverse z FFT (the LS step)
+// Z_FWD / Z_INV: forward / inverse z FFT only; Z_GREEN: contraction only (no FFT)
+// Z_DISP: forward z FFT of a strain, displacement u_hat (3 components), inverse z FFT
+// Z_RHS: forward z FFT of (p, g), -Gamma0_hat : (p_hat + theta_hat), inverse z FFT
+enum ZMode { Z_GAMMA = 0, Z_FWD = 1, Z_INV = 2, Z_DISP = 3, Z_RHS = 4, Z_GREEN = 5 };
+enum InvMode { INV_STORE = 0, INV_CG = 1 };
+enum FinKind { FIN_NONE = 0, FIN_RHS = 1, FIN_BASIC = 2, FIN_CG = 3, FIN_RESID = 4, FIN_ENERGY = 5 };
+
+template <typename Tf, typename T>
+struct FwdArgs {
+  Geo g;
+  int mode, ncomp, in_ncomp;   // components transformed; components per rhs of `in`
+  const uint8_t* phase;
+  const T* mat;                // [n_phase][4] Kelvin eigenvalues: C-C0 (h, dev), C (h, dev)
+  int n_phase;
+  const Tf* in;                // FWD_TAU: strain (nullable); FWD_COPY: field
+  const double* E;             // FWD_TAU: [rhs][6] Kelvin macroscopic strain (nullable)
+  const Tf* r;                 // FWD_CG
+  Tf* p;                       // FWD_CG (read old p, write new p)
+  cx<T>* S;                    // chunk spectrum
+  int rhs0;                    // global rhs index of the chunk's first rhs
+  RhsState* st;                // nullable
+  double* part;                // [rhs][2][ncta] partial sums
+  unsigned* cnt;               // [rhs] tickets
+  const cx<T>* tw_h;
+  const cx<T>* tw_n1;
+  const cx<T>* tw_n2;
+};
+
+template <typename T>
+struct ZArgs {
+  Geo g;
+  int mode, ncomp_in, ncomp_out;
+  int tc_log2;           // tile: 2^tc_log2 consecutive spectrum columns
+  int ntiles;            // ceil(plane_c / 2^tc_log2)
+  int nthr;              // threads per CTA
+  cx<T>* S;
+  int rhs0;
+  const RhsState* st;
+  double lam0, mu0;
+  double scale;          // factor applied with the spectral operator (1/M after a forward FFT)
+  const cx<T>* tw_n3;
+};
+
+template <typename Tf, typename T>
+struct InvArgs {
+  Geo g;
+  int mode, fin, ncomp, out_ncomp;
+  int s_ncomp;           // components per rhs in the spectrum
+  const cx<T>* S;
+  int rhs0;
+  T c0h, c0d;            // C0 Kelvin eigenvalues: 3 lam0 + 2 mu0, 2 mu0
+  Tf* out;               // INV_STORE
+  const Tf* b;           // INV_STORE: added field (nullable)
+  const Tf* sub;         // INV_STORE: subtracted field (nullable)
+  const Tf* prev;        // INV_STORE: previous iterate for the Cauchy difference (nullable)
+  const Tf* p;           // INV_CG
+  Tf* x;                 // INV_CG
+  Tf* r;                 // INV_CG
+  RhsState* st;
+  double* part;
+  unsigned* cnt;
+  const cx<T>* tw_h;
+  const cx<T>* tw_n1;
+  const cx<T>* tw_n2;
+};
+
+template <typename Tf, typename T>
+cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zpass(const ZArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename Tf, typename T>
+cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s);
+
+size_t plane_smem_bytes(const Geo& g, size_t elem);
+size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2);
+// z-pass tiling for ncomp input components: fills tc_log2, ntiles, nthr
+template <typename T>
+void zpass_tiling(ZArgs<T>& a);
+
+}  // namespace hom

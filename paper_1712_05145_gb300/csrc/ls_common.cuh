@@ -1,0 +1,137 @@
+// The Lippmann-Schwinger step on the GPU (Sec. 2 of arXiv:1712.05145, Algorithm 1):
+//
+//   plane_fwd : polarization tau = (C - C0) : (eps + E)         (Eq. auxiliary_problem)
+//               fused with the x-axis R2C and y-axis FFT of one z-plane
+//   zpass     : z-axis FFT, eta_hat = -Gamma0_hat(xi) : tau_hat  (Green operator, Sec. 2)
+//               with eta_hat(0) = 0, inverse z-axis FFT
+//   plane_inv : inverse y FFT and x-axis C2R of one z-plane fused with the update
+//               (fixed-point step, CG vector updates, residuals) and FP64 reductions
+//
+// Strain-like fields are stored in the Kelvin basis of symmetric tensors
+//   k0 = tr(e)/sqrt3, k1 = (e11-e22)/sqrt2, k2 = (e11+e22-2e33)/sqrt6,
+//   k3 = sqrt2 e23, k4 = sqrt2 e13, k5 = sqrt2 e12,
+// an orthonormal basis in which every isotropic stiffness is diagonal (3K on k0, 2mu on
+// k1..k5).  The polarization of component c therefore needs only component c, and
+// one CTA transforms one (rhs, component, z-plane) without touching the others.
+#pragma once
+#include "internal.h"
+
+namespace hom {
+
+constexpr int kEPT = 16;
+
+// ---------------------------------------------------------------------------------
+// small helpers
+template <typename Tf> struct Pair;
+template <> struct Pair<float> { using V = float2; };
+template <> struct Pair<double> { using V = double2; };
+
+template <typename Tf>
+__device__ __forceinline__ void ld2(const Tf* p, Tf& a, Tf& b) {
+  typename Pair<Tf>::V v = *reinterpret_cast<const typename Pair<Tf>::V*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <typename Tf>
+__device__ __forceinline__ void st2(Tf* p, Tf a, Tf b) {
+  typename Pair<Tf>::V v;
+  v.x = a;
+  v.y = b;
+  *reinterpret_cast<typename Pair<Tf>::V*>(p) = v;
+}
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Publishes this block's NQ totals (valid in thread 0 after block_sum_f64) and lets the
+// block that draws the last ticket sum all ncta partials in a fixed order.  Returns
+// true in that block, with the grand totals in thread 0's v.
+template <int NQ>
+__device__ __forceinline__ bool publish_and_collect(double (&v)[NQ], double* part, unsigned* cnt, int ncta, int cta,
+                                    double* sh, int* flag) {
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) part[q * ncta + cta] = v[q];
+    __threadfence();
+    const unsigned t = atomicAdd(cnt, 1u);
+    *flag = (t == (unsigned)(ncta - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = (*flag != 0);
+  if (last) {
+    __threadfence();
+    double s[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+    for (int i = threadIdx.x; i < ncta; i += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) s[q] += __ldcg(part + q * ncta + i);
+    }
+    block_sum_f64<NQ>(s, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] = s[q];
+      *cnt = 0u;
+    }
+  }
+  return last;
+}
+
+__device__ __forceinline__ void finalize_state(int kind, RhsState& s, const double* v, double invM) {
+  switch (kind) {
+    case FIN_ENERGY: {
+      const double pAp = v[0] * invM;
+      s.pAp = pAp;
+      s.alpha = (pAp != 0.0) ? s.rho / pAp : 0.0;
+      if (!isfinite(s.alpha)) { s.status = 2; s.active = 0; }
+      break;
+    }
+    case FIN_CG: {
+      const double rho = v[0] * invM, rr = v[1] * invM;
+      s.beta = (s.rho != 0.0) ? rho / s.rho : 0.0;
+      s.rho = rho;
+      s.res = (s.b2 > 0.0) ? sqrt(rr / s.b2) : 0.0;
+      s.iter += 1;
+      s.restart = 0;
+      if (!isfinite(s.res) || !isfinite(s.beta)) { s.status = 2; s.active = 0; }
+      else if (s.res < s.tol) s.active = 0;
+      else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }
+      break;
+    }
+    case FIN_BASIC: {
+      const double d2 = v[0] * invM;
+      s.res = (s.b2 > 0.0) ? sqrt(d2 / s.b2) : 0.0;
+      s.iter += 1;
+      if (!isfinite(s.res)) { s.status = 2; s.active = 0; }
+      else if (s.res < s.tol) s.active = 0;
+      else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }
+      break;
+    }
+    case FIN_RHS: {
+      s.rho = v[0] * invM;
+      s.b2 = v[1] * invM;
+      s.res = 1.0;
+      s.res_true = 1.0;
+      s.restart = 1;
+      if (!isfinite(s.b2)) { s.status = 2; s.active = 0; }
+      break;
+    }
+    case FIN_RESID: {
+      s.rho = v[0] * invM;
+      s.res_true = (s.b2 > 0.0) ? sqrt(v[1] * invM / s.b2) : 0.0;
+      s.res = s.res_true;
+      s.restart = 1;
+      if (!isfinite(s.res_true)) { s.status = 2; s.active = 0; }
+      break;
+    }
+    default: break;
+  }
+}
+
+template <typename K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+}  // namespace hom

@@ -1,0 +1,196 @@
+// Forward plane pass of the Lippmann-Schwinger step (see ls_common.cuh).
+#include "ls_common.cuh"
+
+namespace hom {
+
+// ---------------------------------------------------------------------------------
+// plane_fwd: one CTA per (z-plane, component, rhs)
+template <typename Tf, typename T, int EPT>
+__global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Geo& g = a.g;
+  const int z = blockIdx.x, c = blockIdx.y, lrhs = blockIdx.z, rhs = a.rhs0 + lrhs;
+  if (a.st != nullptr && a.st[rhs].active == 0) return;
+
+  const int n1 = g.n1, n2 = g.n2, h = g.h, P = g.P;
+  cx<T>* pl = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* nyq = pl + n2 * P;
+  T* tab = reinterpret_cast<T*>(nyq + n2);
+  size_t off = align16((size_t)(n2 * P + n2) * sizeof(cx<T>) + 2 * a.n_phase * sizeof(T));
+  double* sh = reinterpret_cast<double*>(smem_raw + off);
+  int* flag = reinterpret_cast<int*>(sh + 64);
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+
+  if (a.mode != FWD_COPY) {
+    for (int i = tid; i < a.n_phase; i += nthr) {
+      tab[i] = a.mat[i * 4 + (c == 0 ? 0 : 1)];                 // C - C0 eigenvalue
+      tab[a.n_phase + i] = a.mat[i * 4 + (c == 0 ? 2 : 3)];     // C eigenvalue
+    }
+    __syncthreads();
+  }
+
+  const long long plane_sz = (long long)n2 * n1;
+  const long long foff = ((long long)(rhs * a.in_ncomp + c) * g.n3 + z) * plane_sz;
+  const uint8_t* php = a.phase + (long long)z * plane_sz;
+  T acc = (T)0;
+
+  if (a.mode == FWD_TAU) {
+    const T ec = (a.E != nullptr) ? (T)a.E[rhs * 6 + c] : (T)0;
+    for (int row = warp; row < n2; row += nwarp) {
+      for (int c2 = lane; c2 < h; c2 += 32) {
+        const long long o = (long long)row * n1 + 2 * c2;
+        Tf v0 = 0, v1 = 0;
+        if (a.in != nullptr) ld2<Tf>(a.in + foff + o, v0, v1);
+        const uchar2 ph = *reinterpret_cast<const uchar2*>(php + o);
+        pl[row * P + c2] = mk<T>(tab[ph.x] * ((T)v0 + ec), tab[ph.y] * ((T)v1 + ec));
+      }
+    }
+  } else if (a.mode == FWD_CG) {
+    const RhsState& s = a.st[rhs];
+    const T beta = s.restart ? (T)0 : (T)s.beta;
+    for (int row = warp; row < n2; row += nwarp) {
+      for (int c2 = lane; c2 < h; c2 += 32) {
+        const long long o = (long long)row * n1 + 2 * c2;
+        Tf r0, r1, p0, p1;
+        ld2<Tf>(a.r + foff + o, r0, r1);
+        ld2<Tf>(a.p + foff + o, p0, p1);
+        const T q0 = (T)r0 + beta * (T)p0;
+        const T q1 = (T)r1 + beta * (T)p1;
+        st2<Tf>(a.p + foff + o, (Tf)q0, (Tf)q1);
+        const uchar2 ph = *reinterpret_cast<const uchar2*>(php + o);
+        acc += tab[a.n_phase + ph.x] * q0 * q0 + tab[a.n_phase + ph.y] * q1 * q1;
+        pl[row * P + c2] = mk<T>(tab[ph.x] * q0, tab[ph.y] * q1);
+      }
+    }
+  } else {  // FWD_COPY
+    for (int row = warp; row < n2; row += nwarp) {
+      for (int c2 = lane; c2 < h; c2 += 32) {
+        const long long o = (long long)row * n1 + 2 * c2;
+        Tf v0, v1;
+        ld2<Tf>(a.in + foff + o, v0, v1);
+        pl[row * P + c2] = mk<T>((T)v0, (T)v1);
+      }
+    }
+  }
+  __syncthreads();
+
+  // x axis: length-h complex FFT of the packed rows z[n] = x[2n] + i x[2n+1]
+  fft_pencils<T, -1, EPT>(pl, RowAddr{P}, h, n2, a.tw_h);
+
+  // R2C split: X[k] = (Z[k] + conj Z[h-k])/2 - i W^k (Z[k] - conj Z[h-k])/2, W = e^{-2 pi i/n1}.
+  // X[0] and X[n1/2] are real and share slot 0 as X[0] + i X[n1/2].
+  {
+    const int nk = h / 2 + 1;
+    for (int t = tid; t < n2 * nk; t += nthr) {
+      const int row = t % n2, k = t / n2;
+      cx<T>* R = pl + row * P;
+      if (k == 0) {
+        const cx<T> z0 = R[0];
+        R[0] = mk<T>(z0.re + z0.im, z0.re - z0.im);
+      } else if (2 * k == h) {
+        R[k] = conj(R[k]);
+      } else {
+        const cx<T> za = R[k], zb = R[h - k];
+        const cx<T> wa = ldg_cx(a.tw_n1 + k), wb = ldg_cx(a.tw_n1 + (h - k));
+        // X[k]
+        cx<T> e = (za + conj(zb)) * (T)0.5;
+        cx<T> o = mul_i<T, -1>(za - conj(zb)) * (T)0.5;
+        const cx<T> xa = e + cmul(wa, o);
+        // X[h-k]
+        e = (zb + conj(za)) * (T)0.5;
+        o = mul_i<T, -1>(zb - conj(za)) * (T)0.5;
+        const cx<T> xb = e + cmul(wb, o);
+        R[k] = xa;
+        R[h - k] = xb;
+      }
+    }
+  }
+  __syncthreads();
+
+  // y axis: columns kx = 0..h-1 (column 0 carries X[0] + i X[n1/2])
+  fft_pencils<T, -1, EPT>(pl, ColAddr{P}, n2, h, a.tw_n2);
+
+  // separate column 0 into the kx = 0 column (A) and the Nyquist column kx = n1/2 (B):
+  // A[k] = (P[k] + conj P[-k])/2,  B[k] = (P[k] - conj P[-k])/(2i)
+  for (int ky = tid; 2 * ky <= n2; ky += nthr) {
+    const int km = (n2 - ky) % n2;
+    const cx<T> pk = pl[ky * P], pm = pl[km * P];
+    const cx<T> ak = (pk + conj(pm)) * (T)0.5;
+    const cx<T> bk = mul_i<T, -1>(pk - conj(pm)) * (T)0.5;
+    const cx<T> am = (pm + conj(pk)) * (T)0.5;
+    const cx<T> bm = mul_i<T, -1>(pm - conj(pk)) * (T)0.5;
+    pl[ky * P] = ak;
+    nyq[ky] = bk;
+    if (km != ky) {
+      pl[km * P] = am;
+      nyq[km] = bm;
+    }
+  }
+  __syncthreads();
+
+  cx<T>* Sp = a.S + ((long long)(lrhs * a.ncomp + c) * g.n3 + z) * g.plane_c;
+  for (int row = warp; row < n2; row += nwarp)
+    for (int col = lane; col < h; col += 32) Sp[(long long)row * h + col] = pl[row * P + col];
+  for (int ky = tid; ky < n2; ky += nthr) Sp[(long long)n2 * h + ky] = nyq[ky];
+
+  if (a.mode == FWD_CG) {
+    double v[1] = {(double)acc};
+    block_sum_f64<1>(v, sh);
+    const int ncta = a.ncomp * g.n3;
+    if (publish_and_collect<1>(v, a.part + (long long)rhs * 2 * ncta, a.cnt + rhs, ncta, c * g.n3 + z,
+                               sh, flag)) {
+      if (threadIdx.x == 0) finalize_state(FIN_ENERGY, a.st[rhs], v, 1.0 / (double)g.M);
+    }
+  }
+}
+
+size_t plane_smem_bytes(const Geo& g, size_t elem) {
+  size_t b = (size_t)(g.n2 * g.P + g.n2) * elem + 2 * 256 * elem;
+  b = (b + 15) & ~size_t(15);
+  return b + 64 * sizeof(double) + 16;
+}
+size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2) {
+  return (size_t)ncomp * g.n3 * ((size_t)1 << tc_log2) * elem;
+}
+
+// Widest power-of-two tile (<= 16 columns) whose pencils fit kEPT elements per thread
+// at <= 512 threads and <= 64 KB of shared memory.
+template <typename T>
+void zpass_tiling(ZArgs<T>& a) {
+  const size_t elem = sizeof(cx<T>);
+  int lg = 4;
+  while (lg > 0 && ((size_t)a.ncomp_in * a.g.n3 * ((size_t)1 << lg) > (size_t)kEPT * 512 ||
+                    zpass_smem_bytes(a.g, elem, a.ncomp_in, lg) > 64 * 1024))
+    --lg;
+  a.tc_log2 = lg;
+  const long long tc = 1LL << lg;
+  a.ntiles = (int)((a.g.plane_c + tc - 1) / tc);
+  const long long e = (long long)a.ncomp_in * a.g.n3 * tc;
+  int thr = (int)((e + kEPT - 1) / kEPT);
+  thr = ((thr + 31) / 32) * 32;
+  if (thr < 128) thr = 128;
+  a.nthr = thr;
+}
+template void zpass_tiling<float>(ZArgs<float>&);
+template void zpass_tiling<double>(ZArgs<double>&);
+
+template <typename Tf, typename T>
+cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) {
+  if ((long long)a.g.n2 * a.g.h > (long long)kEPT * a.g.thr_plane || a.g.thr_plane > 512 || a.n_phase > 256)
+    return cudaErrorInvalidValue;
+  const size_t smem = plane_smem_bytes(a.g, sizeof(cx<T>));
+  auto k = plane_fwd_kernel<Tf, T, kEPT>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.g.n3, a.ncomp, nrhs);
+  k<<<grid, a.g.thr_plane, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_plane_fwd<float, float>(const FwdArgs<float, float>&, int, cudaStream_t);
+template cudaError_t launch_plane_fwd<double, double>(const FwdArgs<double, double>&, int, cudaStream_t);
+template cudaError_t launch_plane_fwd<float, double>(const FwdArgs<float, double>&, int, cudaStream_t);
+
+}  // namespace hom

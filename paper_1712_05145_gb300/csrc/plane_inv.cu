@@ -1,0 +1,142 @@
+// Inverse plane pass of the Lippmann-Schwinger step with the solver epilogues.
+#include "ls_common.cuh"
+
+namespace hom {
+
+// ---------------------------------------------------------------------------------
+// plane_inv: one CTA per (z-plane, component, rhs)
+template <typename Tf, typename T, int EPT>
+__global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) {
+  const int s_ncomp = a.s_ncomp;
+  const T c0h = a.c0h, c0d = a.c0d;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Geo& g = a.g;
+  const int z = blockIdx.x, c = blockIdx.y, lrhs = blockIdx.z, rhs = a.rhs0 + lrhs;
+  if (a.st != nullptr && a.st[rhs].active == 0) return;
+  const int n1 = g.n1, n2 = g.n2, h = g.h, P = g.P;
+  cx<T>* pl = reinterpret_cast<cx<T>*>(smem_raw);
+  size_t off = align16((size_t)(n2 * P + n2) * sizeof(cx<T>));
+  double* sh = reinterpret_cast<double*>(smem_raw + off);
+  int* flag = reinterpret_cast<int*>(sh + 64);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+
+  const cx<T>* Sp = a.S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
+  const long long nmain = (long long)n2 * h;
+  for (int row = warp; row < n2; row += nwarp) {
+    for (int col = lane; col < h; col += 32) {
+      cx<T> v = Sp[(long long)row * h + col];
+      if (col == 0) {  // pack kx = 0 (A) and kx = n1/2 (B) as A + i B
+        const cx<T> b = Sp[nmain + row];
+        v = mk<T>(v.re - b.im, v.im + b.re);
+      }
+      pl[row * P + col] = v;
+    }
+  }
+  __syncthreads();
+
+  fft_pencils<T, +1, EPT>(pl, ColAddr{P}, n2, h, a.tw_n2);
+
+  // C2R merge: Z[k] = X[k] + conj X[h-k] + i W^{-k} (X[k] - conj X[h-k]),  W = e^{-2 pi i/n1};
+  // slot 0 holds X[0] + i X[n1/2]
+  {
+    const int nk = h / 2 + 1;
+    for (int t = tid; t < n2 * nk; t += nthr) {
+      const int row = t % n2, k = t / n2;
+      cx<T>* R = pl + row * P;
+      if (k == 0) {
+        const T x0 = R[0].re, xn = R[0].im;
+        R[0] = mk<T>(x0 + xn, x0 - xn);
+      } else if (2 * k == h) {
+        R[k] = conj(R[k]) * (T)2;
+      } else {
+        const cx<T> xa = R[k], xb = R[h - k];
+        const cx<T> wa = conj(ldg_cx(a.tw_n1 + k)), wb = conj(ldg_cx(a.tw_n1 + (h - k)));
+        const cx<T> za = (xa + conj(xb)) + mul_i<T, 1>(cmul(wa, xa - conj(xb)));
+        const cx<T> zb = (xb + conj(xa)) + mul_i<T, 1>(cmul(wb, xb - conj(xa)));
+        R[k] = za;
+        R[h - k] = zb;
+      }
+    }
+  }
+  __syncthreads();
+
+  fft_pencils<T, +1, EPT>(pl, RowAddr{P}, h, n2, a.tw_h);
+
+  // epilogue on the real plane: x[2n] = Re z[n], x[2n+1] = Im z[n]
+  const long long plane_sz = (long long)n2 * n1;
+  T q0 = 0, q1 = 0;
+  if (a.mode == INV_STORE) {
+    const long long foff = ((long long)(rhs * a.out_ncomp + c) * g.n3 + z) * plane_sz;
+    const T cw = (c == 0) ? c0h : c0d;
+    for (int row = warp; row < n2; row += nwarp) {
+      for (int c2 = lane; c2 < h; c2 += 32) {
+        const long long o = foff + (long long)row * n1 + 2 * c2;
+        const cx<T> e = pl[row * P + c2];
+        T v0 = e.re, v1 = e.im;
+        if (a.b != nullptr) { Tf b0, b1; ld2<Tf>(a.b + o, b0, b1); v0 += (T)b0; v1 += (T)b1; }
+        if (a.sub != nullptr) { Tf s0, s1; ld2<Tf>(a.sub + o, s0, s1); v0 -= (T)s0; v1 -= (T)s1; }
+        if (a.fin == FIN_BASIC) {
+          Tf p0, p1;
+          ld2<Tf>(a.prev + o, p0, p1);
+          const T d0 = v0 - (T)p0, d1 = v1 - (T)p1;
+          q0 += d0 * d0 + d1 * d1;
+        } else {
+          q0 += cw * (v0 * v0 + v1 * v1);
+        }
+        q1 += v0 * v0 + v1 * v1;
+        st2<Tf>(a.out + o, (Tf)v0, (Tf)v1);
+      }
+    }
+  } else {  // INV_CG: q = p - eta, x += alpha p, r -= alpha q
+    const long long foff = ((long long)(rhs * 6 + c) * g.n3 + z) * plane_sz;
+    const T alpha = (T)a.st[rhs].alpha;
+    const T cw = (c == 0) ? c0h : c0d;
+    for (int row = warp; row < n2; row += nwarp) {
+      for (int c2 = lane; c2 < h; c2 += 32) {
+        const long long o = foff + (long long)row * n1 + 2 * c2;
+        const cx<T> e = pl[row * P + c2];
+        Tf p0, p1, x0, x1, r0, r1;
+        ld2<Tf>(a.p + o, p0, p1);
+        ld2<Tf>(a.x + o, x0, x1);
+        ld2<Tf>(a.r + o, r0, r1);
+        const T qa = (T)p0 - e.re, qb = (T)p1 - e.im;
+        const T xa = (T)x0 + alpha * (T)p0, xb = (T)x1 + alpha * (T)p1;
+        const T ra = (T)r0 - alpha * qa, rb = (T)r1 - alpha * qb;
+        st2<Tf>(a.x + o, (Tf)xa, (Tf)xb);
+        st2<Tf>(a.r + o, (Tf)ra, (Tf)rb);
+        q0 += cw * (ra * ra + rb * rb);
+        q1 += ra * ra + rb * rb;
+      }
+    }
+  }
+
+  if (a.fin != FIN_NONE) {
+    double v[2] = {(double)q0, (double)q1};
+    block_sum_f64<2>(v, sh);
+    const int ncta = a.ncomp * g.n3;
+    if (publish_and_collect<2>(v, a.part + (long long)rhs * 2 * ncta, a.cnt + rhs, ncta, c * g.n3 + z,
+                               sh, flag)) {
+      if (threadIdx.x == 0) finalize_state(a.fin, a.st[rhs], v, 1.0 / (double)g.M);
+    }
+  }
+}
+
+template <typename Tf, typename T>
+cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s) {
+  if ((long long)a.g.n2 * a.g.h > (long long)kEPT * a.g.thr_plane || a.g.thr_plane > 512)
+    return cudaErrorInvalidValue;
+  const size_t smem = plane_smem_bytes(a.g, sizeof(cx<T>));
+  auto k = plane_inv_kernel<Tf, T, kEPT>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.g.n3, a.ncomp, nrhs);
+  k<<<grid, a.g.thr_plane, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_plane_inv<float, float>(const InvArgs<float, float>&, int, cudaStream_t);
+template cudaError_t launch_plane_inv<double, double>(const InvArgs<double, double>&, int, cudaStream_t);
+template cudaError_t launch_plane_inv<float, double>(const InvArgs<float, double>&, int, cudaStream_t);
+
+}  // namespace hom

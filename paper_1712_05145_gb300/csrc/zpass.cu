@@ -1,0 +1,167 @@
+// z-pencil pass of the Lippmann-Schwinger step: z FFTs and the Green contraction.
+#include "ls_common.cuh"
+
+namespace hom {
+
+// ---------------------------------------------------------------------------------
+// zpass: one CTA per (tile of 2^tc_log2 spectrum columns, rhs)
+// Kelvin components -> symmetric tensor (t11, t22, t33, t23, t13, t12)
+template <typename T>
+__device__ __forceinline__ void kelvin_to_tensor(const cx<T>* k, cx<T>* t) {
+  const T r3 = (T)0.57735026918962576451, r2 = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637;
+  t[0] = k[0] * r3 + k[1] * r2 + k[2] * r6;
+  t[1] = k[0] * r3 - k[1] * r2 + k[2] * r6;
+  t[2] = k[0] * r3 - k[2] * ((T)2 * r6);
+  t[3] = k[3] * r2;
+  t[4] = k[4] * r2;
+  t[5] = k[5] * r2;
+}
+
+// w = t xi for a symmetric tensor t
+template <typename T>
+__device__ __forceinline__ void tensor_dot_xi(const cx<T>* t, T x1, T x2, T x3, cx<T>& w1, cx<T>& w2, cx<T>& w3) {
+  w1 = t[0] * x1 + t[5] * x2 + t[4] * x3;
+  w2 = t[5] * x1 + t[1] * x2 + t[3] * x3;
+  w3 = t[4] * x1 + t[3] * x2 + t[2] * x3;
+}
+
+// eta_hat = -Gamma0_hat(xi) : tau_hat in Kelvin components, given w = tau_hat xi.
+// Gamma0_hat : tau_hat = v (x) xi + xi (x) v with
+// v = w / (2 mu0 |xi|^2) - (lam0 + mu0) / (2 mu0 (lam0 + 2 mu0)) (xi . w) xi / |xi|^4,
+// the four-index formula of Sec. 2 contracted with a symmetric tau_hat.
+template <typename T>
+__device__ __forceinline__ void green_from_w(cx<T>* k, cx<T> w1, cx<T> w2, cx<T> w3, T x1, T x2, T x3, T c1,
+                                             T c2h, T scale) {
+  const T r3 = (T)0.57735026918962576451, r2 = (T)0.70710678118654752440,
+          r6 = (T)0.40824829046386301637, s2 = (T)1.41421356237309504880;
+  const T q = x1 * x1 + x2 * x2 + x3 * x3;
+  if (q == (T)0) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) k[i] = mk<T>(0, 0);
+    return;
+  }
+  const cx<T> s = w1 * x1 + w2 * x2 + w3 * x3;
+  const T iq = (T)1 / q;
+  const T a1 = c1 * iq * scale;
+  const T a2 = c2h * iq * iq * scale;
+  const cx<T> v1 = w1 * a1 - s * (a2 * x1);
+  const cx<T> v2 = w2 * a1 - s * (a2 * x2);
+  const cx<T> v3 = w3 * a1 - s * (a2 * x3);
+  const cx<T> e11 = v1 * ((T)-2 * x1), e22 = v2 * ((T)-2 * x2), e33 = v3 * ((T)-2 * x3);
+  k[0] = (e11 + e22 + e33) * r3;
+  k[1] = (e11 - e22) * r2;
+  k[2] = (e11 + e22 - e33 * (T)2) * r6;
+  k[3] = (v2 * x3 + v3 * x2) * (-s2);
+  k[4] = (v1 * x3 + v3 * x1) * (-s2);
+  k[5] = (v1 * x2 + v2 * x1) * (-s2);
+}
+
+// integer wave number of DFT index j on an axis of length n, Nyquist -> 0 (discrete derivative)
+__device__ __forceinline__ int wave(int j, int n) {
+  int k = (j >= (n + 1) / 2) ? j - n : j;
+  if ((n & 1) == 0 && 2 * j == n) k = 0;
+  return k;
+}
+
+template <typename T, int EPT>
+__global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
+  const int tc_log2 = a.tc_log2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Geo& g = a.g;
+  const int tile = blockIdx.x, lrhs = blockIdx.y, rhs = a.rhs0 + lrhs;
+  if (a.st != nullptr && a.st[rhs].active == 0) return;
+  const int TC = 1 << tc_log2, n3 = g.n3;
+  const long long f0 = (long long)tile * TC;
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int cstride = n3 * TC;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  cx<T>* Sr = a.S + (long long)lrhs * a.ncomp_in * n3 * g.plane_c;
+
+  for (int e = tid; e < a.ncomp_in * n3 * TC; e += nthr) {
+    const int tc = e & (TC - 1), row = e >> tc_log2;
+    const long long f = f0 + tc;
+    buf[e] = (f < g.plane_c) ? Sr[(long long)row * g.plane_c + f] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  const ZAddr za{tc_log2, cstride, TC};
+  if (a.mode != Z_INV && a.mode != Z_GREEN) fft_pencils<T, -1, EPT>(buf, za, n3, a.ncomp_in * TC, a.tw_n3);
+
+  if (a.mode == Z_GAMMA || a.mode == Z_GREEN || a.mode == Z_DISP || a.mode == Z_RHS) {
+    const T c1 = (T)(1.0 / (2.0 * a.mu0));
+    const T c2h = (T)((a.lam0 + a.mu0) / (2.0 * a.mu0 * (a.lam0 + 2.0 * a.mu0)));
+    const T scale = (T)a.scale;
+    const long long nmain = (long long)g.n2 * g.h;
+    for (int t = tid; t < n3 * TC; t += nthr) {
+      const int tc = t & (TC - 1), n = t >> tc_log2;
+      const long long f = f0 + tc;
+      if (f >= g.plane_c) continue;
+      int kx, ky;
+      if (f < nmain) { ky = (int)(f / g.h); kx = (int)(f - (long long)ky * g.h); }
+      else { ky = (int)(f - nmain); kx = g.h; }
+      // discrete wave vector: Nyquist components taken as 0
+      const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
+      const T x2 = (T)(wave(ky, g.n2) * g.xs2);
+      const T x3 = (T)(wave(n, n3) * g.xs3);
+      const int e0 = n * TC + tc;
+      cx<T> k[6], tt[6], w1, w2, w3;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) k[i] = buf[i * cstride + e0];
+      kelvin_to_tensor<T>(k, tt);
+      tensor_dot_xi<T>(tt, x1, x2, x3, w1, w2, w3);
+      if (a.mode == Z_DISP) {
+        // u_hat = -i (2 w - xi (xi . w) / |xi|^2) / |xi|^2 for eps_hat = i sym(xi (x) u_hat)
+        const T q = x1 * x1 + x2 * x2 + x3 * x3;
+        cx<T> u[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
+        if (q != (T)0) {
+          const cx<T> s = w1 * x1 + w2 * x2 + w3 * x3;
+          const T iq = (T)1 / q;
+          const T b = iq * scale;
+          u[0] = mul_i<T, -1>(w1 * ((T)2 * b) - s * (x1 * iq * b));
+          u[1] = mul_i<T, -1>(w2 * ((T)2 * b) - s * (x2 * iq * b));
+          u[2] = mul_i<T, -1>(w3 * ((T)2 * b) - s * (x3 * iq * b));
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) buf[i * cstride + e0] = u[i];
+      } else {
+        if (a.mode == Z_RHS) {
+          // (p_hat + theta_hat) xi = p_hat xi - i g_hat, since i theta_hat xi = g_hat (Sec. 3)
+          w1 = w1 - mul_i<T, 1>(buf[6 * cstride + e0]);
+          w2 = w2 - mul_i<T, 1>(buf[7 * cstride + e0]);
+          w3 = w3 - mul_i<T, 1>(buf[8 * cstride + e0]);
+        }
+        green_from_w<T>(k, w1, w2, w3, x1, x2, x3, c1, c2h, scale);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) buf[i * cstride + e0] = k[i];
+      }
+    }
+    __syncthreads();
+  }
+
+  if (a.mode != Z_FWD && a.mode != Z_GREEN) fft_pencils<T, +1, EPT>(buf, za, n3, a.ncomp_out * TC, a.tw_n3);
+
+  for (int e = tid; e < a.ncomp_out * n3 * TC; e += nthr) {
+    const int tc = e & (TC - 1), row = e >> tc_log2;
+    const long long f = f0 + tc;
+    if (f < g.plane_c) Sr[(long long)row * g.plane_c + f] = buf[e];
+  }
+}
+
+template <typename T>
+cudaError_t launch_zpass(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
+  // every pencil element must have a thread slot (kEPT per thread, <= 512 threads)
+  if ((long long)a.ncomp_in * a.g.n3 * (1LL << a.tc_log2) > (long long)kEPT * a.nthr || a.nthr > 512 ||
+      a.ncomp_out > a.ncomp_in)
+    return cudaErrorInvalidValue;
+  const size_t smem = zpass_smem_bytes(a.g, sizeof(cx<T>), a.ncomp_in, a.tc_log2);
+  auto k = zpass_kernel<T, kEPT>;
+  cudaError_t e = set_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.ntiles, nrhs);
+  k<<<grid, a.nthr, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_zpass<float>(const ZArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_zpass<double>(const ZArgs<double>&, int, cudaStream_t);
+
+}  // namespace hom

@@ -1,0 +1,265 @@
+"""Thin Python binding of libhom (include/hom.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts Python
+arguments to pointers and sizes.  Device buffers are torch CUDA tensors (float64),
+host buffers numpy arrays.  The functions keep the C names (``hom_create``,
+``hom_solve``, ...); ``Homogenization`` wraps a handle for convenience.
+
+Importing this module does not need a GPU; loading the library fails loudly if
+``libhom.so`` has not been built (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libhom.so")
+
+HOM_OK = 0
+HOM_ERR_ARG = 1
+HOM_ERR_SIZE = 2
+HOM_ERR_NOMEM = 3
+HOM_ERR_NOT_CONVERGED = 4
+HOM_ERR_ORDER = 5
+HOM_ERR_NUMERIC = 6
+HOM_ERR_TIMEOUT = 7
+HOM_ERR_CUDA = 8
+
+HOM_FP64 = 0
+HOM_FP32_REFINE = 1
+HOM_BASIC = 0
+HOM_CG = 1
+HOM_FIELD_STRAIN = 0
+HOM_FIELD_DISPLACEMENT = 1
+HOM_FIELD_STRESS = 2
+
+EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
+            "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply",
+            "hom_device_bytes", "hom_last_error", "hom_status_string", "hom_destroy"]
+
+
+class hom_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("scheme", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
+                ("l2_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class hom_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("rel_residual_fp64", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "refinements": self.refinements, "status": self.status,
+                "rel_residual": self.rel_residual, "rel_residual_fp64": self.rel_residual_fp64}
+
+
+class HomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status_name(status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Loads libhom.so (raises if it is missing: build it with paper_1712_05145_gb300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libhom.so not found at %s; run `python -m paper_1712_05145_gb300.build`" % p)
+    lib = ctypes.CDLL(p)
+    V, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.hom_default_options.argtypes = [ctypes.POINTER(hom_options)]
+    lib.hom_default_options.restype = None
+    lib.hom_create.argtypes = [ctypes.POINTER(ctypes.c_int32), V, I32, V, D, D, ctypes.POINTER(hom_options),
+                               ctypes.POINTER(V)]
+    lib.hom_create.restype = I32
+    lib.hom_solve.argtypes = [V, I32, I32, V, D, V]
+    lib.hom_solve.restype = I32
+    lib.hom_effective.argtypes = [V, I32, V]
+    lib.hom_effective.restype = I32
+    lib.hom_get_field.argtypes = [V, I32, I32, I32, V, I32]
+    lib.hom_get_field.restype = I32
+    lib.hom_ls_apply.argtypes = [V, I32, V, V, V]
+    lib.hom_ls_apply.restype = I32
+    lib.hom_fft_forward.argtypes = [V, I32, V, V]
+    lib.hom_fft_forward.restype = I32
+    lib.hom_fft_inverse.argtypes = [V, I32, V, V]
+    lib.hom_fft_inverse.restype = I32
+    lib.hom_green_apply.argtypes = [V, I32, V, V]
+    lib.hom_green_apply.restype = I32
+    lib.hom_device_bytes.argtypes = [V]
+    lib.hom_device_bytes.restype = I64
+    lib.hom_last_error.argtypes = [V]
+    lib.hom_last_error.restype = ctypes.c_char_p
+    lib.hom_status_string.argtypes = [I32]
+    lib.hom_status_string.restype = ctypes.c_char_p
+    lib.hom_destroy.argtypes = [V]
+    lib.hom_destroy.restype = None
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_name(s):
+    return load_library().hom_status_string(int(s)).decode()
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def _check(h, s):
+    if s != HOM_OK:
+        msg = load_library().hom_last_error(h).decode() if h else ""
+        raise HomError(s, msg)
+
+
+# ---- C-named functions ---------------------------------------------------------------
+def hom_default_options():
+    o = hom_options()
+    load_library().hom_default_options(ctypes.byref(o))
+    return o
+
+
+def hom_create(grid, phase, lame, lambda0, mu0, options=None):
+    """Returns a handle (ctypes c_void_p).  ``phase`` uint8 [N3][N2][N1] numpy or torch."""
+    lib = load_library()
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    lame = np.ascontiguousarray(lame, dtype=np.float64)
+    if isinstance(phase, np.ndarray):
+        phase = np.ascontiguousarray(phase, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    opt = options if options is not None else hom_default_options()
+    s = lib.hom_create(g, _ptr(phase), int(lame.shape[0]), _ptr(lame), float(lambda0), float(mu0),
+                       ctypes.byref(opt), ctypes.byref(h))
+    if s != HOM_OK:
+        raise HomError(s, "hom_create rejected grid=%s" % (tuple(grid),))
+    return h
+
+
+def hom_solve(h, order, tol, loads=None):
+    """Returns a list of per-load info dicts; raises HomError on any failure except
+    non-convergence, which is reported through each load's status."""
+    lib = load_library()
+    nl = {0: 6, 1: 18, 2: 36}[order] if loads is None else int(np.asarray(loads).shape[0])
+    arr = None
+    if loads is not None:
+        arr = np.ascontiguousarray(loads, dtype=np.float64).reshape(nl, 6)
+    info = (hom_solve_info * nl)()
+    s = lib.hom_solve(h, int(order), nl, _ptr(arr), float(tol), ctypes.cast(info, ctypes.c_void_p))
+    if s not in (HOM_OK, HOM_ERR_NOT_CONVERGED):
+        _check(h, s)
+    return [i.as_dict() for i in info]
+
+
+def hom_effective(h, order, nloads):
+    out = np.zeros((6, nloads), dtype=np.float64)
+    _check(h, load_library().hom_effective(h, int(order), _ptr(out)))
+    return out
+
+
+def hom_get_field(h, order, load, kind, dst, dst_on_device):
+    _check(h, load_library().hom_get_field(h, int(order), int(load), int(kind), _ptr(dst), int(dst_on_device)))
+    return dst
+
+
+def hom_ls_apply(h, nrhs, eps_in, E, eps_out):
+    E = None if E is None else np.ascontiguousarray(E, dtype=np.float64).reshape(nrhs, 6)
+    _check(h, load_library().hom_ls_apply(h, int(nrhs), _ptr(eps_in), _ptr(E), _ptr(eps_out)))
+    return eps_out
+
+
+def hom_fft_forward(h, nfield, f, fhat):
+    _check(h, load_library().hom_fft_forward(h, int(nfield), _ptr(f), _ptr(fhat)))
+    return fhat
+
+
+def hom_fft_inverse(h, nfield, fhat, f):
+    _check(h, load_library().hom_fft_inverse(h, int(nfield), _ptr(fhat), _ptr(f)))
+    return f
+
+
+def hom_green_apply(h, nrhs, tau_hat, eta_hat):
+    _check(h, load_library().hom_green_apply(h, int(nrhs), _ptr(tau_hat), _ptr(eta_hat)))
+    return eta_hat
+
+
+def hom_device_bytes(h):
+    return int(load_library().hom_device_bytes(h))
+
+
+def hom_last_error(h):
+    return load_library().hom_last_error(h).decode()
+
+
+def hom_destroy(h):
+    if h:
+        load_library().hom_destroy(h)
+
+
+# ---- convenience wrapper ---------------------------------------------------------------
+class Homogenization:
+    """One RVE on the GPU.  ``ms`` is a synthetic.Microstructure (or anything with
+    .phase, .lame, .lam0, .mu0)."""
+
+    NLOADS = {0: 6, 1: 18, 2: 36}
+
+    def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
+                 max_refine=6, rhs_chunk=0, l2_budget_bytes=64 << 20, stream=None, lam0=None, mu0=None):
+        n3, n2, n1 = ms.phase.shape
+        self.grid = (n1, n2, n3)
+        self.M = n1 * n2 * n3
+        opt = hom_default_options()
+        opt.precision = precision
+        opt.scheme = scheme
+        opt.max_iter = max_iter
+        opt.check_every = check_every
+        opt.max_refine = max_refine
+        opt.rhs_chunk = rhs_chunk
+        opt.l2_budget_bytes = l2_budget_bytes
+        opt.cuda_stream = stream
+        self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
+                            ms.mu0 if mu0 is None else mu0, opt)
+        self.nloads = {}
+
+    def close(self):
+        if self.h:
+            hom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, order, tol, loads=None):
+        info = hom_solve(self.h, order, tol, loads)
+        self.nloads[order] = len(info)
+        return info
+
+    def effective(self, order):
+        return hom_effective(self.h, order, self.nloads[order])
+
+    def field(self, order, load, kind=HOM_FIELD_STRAIN, device=False):
+        nc = 3 if kind == HOM_FIELD_DISPLACEMENT else 6
+        n1, n2, n3 = self.grid
+        if device:
+            import torch
+            dst = torch.empty((nc, n3, n2, n1), dtype=torch.float64, device="cuda")
+            return hom_get_field(self.h, order, load, kind, dst, 1)
+        dst = np.empty((nc, n3, n2, n1), dtype=np.float64)
+        return hom_get_field(self.h, order, load, kind, dst, 0)

@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every entry point its header declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1712_05145_gb300 import build, hom
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return hom.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "hom.h")).read()
+    return sorted(set(re.findall(r"HOM_API\s+[\w\s\*]+?\b(hom_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_bound_functions():
+    assert declared_symbols() == sorted(hom.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_defaults(lib):
+    assert hom.status_name(hom.HOM_ERR_SIZE) == "HOM_ERR_SIZE"
+    o = hom.hom_default_options()
+    assert o.precision == hom.HOM_FP32_REFINE and o.scheme == hom.HOM_CG and o.check_every == 8
+
+
+@pytest.mark.parametrize("grid", [(7, 8, 8), (10, 8, 8), (8, 5, 8), (8, 8, 10), (2, 8, 8), (1024, 32, 32)])
+def test_unsupported_grids_rejected_before_any_cuda_call(lib, grid):
+    n1, n2, n3 = grid
+    phase = np.zeros((n3, n2, n1), dtype=np.uint8)
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_create(grid, phase, np.array([[1.0, 1.0]]), 1.0, 1.0)
+    assert e.value.status == hom.HOM_ERR_SIZE
+
+
+def test_bad_reference_medium_rejected(lib):
+    phase = np.zeros((8, 8, 8), dtype=np.uint8)
+    for lam0, mu0 in [(1.0, 0.0), (-2.0, 1.0)]:
+        with pytest.raises(hom.HomError) as e:
+            hom.hom_create((8, 8, 8), phase, np.array([[1.0, 1.0]]), lam0, mu0)
+        assert e.value.status == hom.HOM_ERR_ARG
+
+
+def test_null_handle_calls(lib):
+    assert lib.hom_solve(None, 0, 6, None, 1e-6, None) == hom.HOM_ERR_ARG
+    assert lib.hom_effective(None, 0, None) == hom.HOM_ERR_ARG
+    assert lib.hom_device_bytes(None) == 0
+    lib.hom_destroy(None)

@@ -1,0 +1,79 @@
+"""GPU parity of the higher-order problems (orders 1 and 2, the paper's alpha = 2 and 3)."""
+import numpy as np
+import pytest
+
+from oracle.hierarchy import Hierarchy
+from oracle.lippmann_schwinger import Problem
+from oracle.tensors import tensor_to_mandel
+from paper_1712_05145_gb300 import synthetic
+from tests.helpers import TOL, TOL_EFF, random_phase, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def asym_cell():
+    g = (8, 12, 6)
+    return synthetic.Microstructure(random_phase(g, 3, 21, p=[0.5, 0.3, 0.2]),
+                                    np.array([[1.0, 1.0], [6.0, 4.0], [0.3, 0.2]]), 3.0, 2.0)
+
+
+@pytest.fixture(scope="module")
+def oracle_asym():
+    ms = asym_cell()
+    h = Hierarchy(Problem(ms.phase, ms.lame, ms.lam0, ms.mu0), tol=1e-12)
+    h.order1()
+    h.order2()
+    h.order3()
+    return ms, h
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_orders_0_1_2_match_oracle(oracle_asym, precision):
+    from paper_1712_05145_gb300 import hom
+    ms, oh = oracle_asym
+    H = hom.Homogenization(ms, precision=precision)
+    tol = 1e-12 if precision == 0 else 1e-7
+    for order in (0, 1, 2):
+        info = H.solve(order, tol)
+        assert all(i["status"] == 0 for i in info), (order, info)
+    tol_f = TOL[precision] * (1 if precision == 0 else 5)
+    assert rel_err(H.effective(0), oh.c_eff) < TOL_EFF[precision]
+    assert rel_err(H.effective(1), oh.d1) < TOL_EFF[precision] * 10
+    assert rel_err(H.effective(2), oh.d2) < TOL_EFF[precision] * 10
+    for a in (0, 4):
+        assert rel_err(H.field(0, a, hom.HOM_FIELD_DISPLACEMENT), oh.chi[a]) < tol_f
+    for L in (0, 7, 17):
+        a, k = divmod(L, 3)
+        assert rel_err(H.field(1, L), tensor_to_mandel(oh.eps2[(a, k)])) < tol_f, L
+        assert rel_err(H.field(1, L, hom.HOM_FIELD_DISPLACEMENT), oh.u2[(a, k)]) < tol_f, L
+    for L in (0, 11, 35):
+        a, P = divmod(L, 6)
+        assert rel_err(H.field(2, L), tensor_to_mandel(oh.eps3[(a, P)])) < tol_f, L
+    H.close()
+
+
+def test_order1_vanishes_for_centrosymmetric_cell():
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(16)
+    H = hom.Homogenization(ms, precision=0)
+    H.solve(0, 1e-12)
+    info = H.solve(1, 1e-12)
+    assert all(i["status"] == 0 for i in info)
+    d1 = H.effective(1)
+    assert np.abs(d1).max() < 1e-9 * np.abs(H.effective(0)).max()
+    assert np.abs(H.field(1, 4)).max() > 1e-4
+    H.close()
+
+
+def test_order_dependencies_enforced():
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(8)
+    H = hom.Homogenization(ms, precision=0)
+    with pytest.raises(hom.HomError) as e:
+        H.solve(1, 1e-8)
+    assert e.value.status == hom.HOM_ERR_ORDER
+    H.solve(0, 1e-10, loads=np.eye(6)[:2])
+    with pytest.raises(hom.HomError):
+        H.solve(1, 1e-8)
+    H.close()

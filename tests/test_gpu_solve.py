@@ -1,0 +1,124 @@
+"""GPU parity of the order-0 solvers (Basic Scheme, CG, FP32 + FP64 refinement) and C_eff."""
+import numpy as np
+import pytest
+
+from oracle import closed_forms
+from oracle.lippmann_schwinger import Problem
+from oracle.tensors import tensor_to_mandel, unit_mandel_load
+from paper_1712_05145_gb300 import synthetic
+from tests.helpers import TOL, TOL_EFF, random_phase, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def oracle_order0(ms, tol=1e-12):
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    sols, c_eff = pb.solve_order0(tol=tol, scheme="cg")
+    return [tensor_to_mandel(s) for s in sols], c_eff
+
+
+@pytest.mark.parametrize("precision,scheme", [(0, 0), (0, 1), (1, 1)])
+def test_order0_sphere16_fields_and_ceff(precision, scheme):
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(16)
+    ref_f, ref_c = oracle_order0(ms)
+    H = hom.Homogenization(ms, precision=precision, scheme=scheme)
+    tol = 1e-12 if precision == 0 else 1e-7
+    info = H.solve(0, tol)
+    assert all(i["status"] == 0 for i in info), info
+    assert all(i["rel_residual_fp64"] < tol for i in info), info
+    c = H.effective(0)
+    assert rel_err(c, ref_c) < TOL_EFF[precision]
+    for a in range(6):
+        assert rel_err(H.field(0, a), ref_f[a]) < TOL[precision], a
+    H.close()
+
+
+def test_config_c1_sphere32_basic_scheme_fp64():
+    """32^3 sphere, f = 0.2, (1,1)/(10,10), C0 = mean, Basic Scheme FP64, E = e11."""
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(32)
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    b = pb.rhs(unit_mandel_load(0))
+    ref, _, _ = pb.cg(b, 1e-12)
+    ref_m = tensor_to_mandel(ref)
+    ref_col = pb.mean_stress(ref, unit_mandel_load(0))
+    H = hom.Homogenization(ms, precision=hom.HOM_FP64, scheme=hom.HOM_BASIC, max_iter=5000)
+    info = H.solve(0, 1e-12, loads=np.eye(6)[:1])
+    assert info[0]["status"] == 0 and info[0]["rel_residual_fp64"] < 1e-11
+    assert rel_err(H.field(0, 0), ref_m) < 1e-10
+    assert rel_err(H.effective(0)[:, 0], ref_col) < 1e-9
+    # the configuration's own stopping tolerance
+    info = H.solve(0, 1e-8, loads=np.eye(6)[:1])
+    assert info[0]["status"] == 0 and 50 < info[0]["iterations"] < 200
+    assert rel_err(H.effective(0)[:, 0], ref_col) < 1e-6
+    H.close()
+
+
+@pytest.mark.parametrize("precision,scheme", [(0, 0), (0, 1), (1, 1)])
+def test_config_c1_laminate32_closed_form(precision, scheme):
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.laminate((32, 32, 32))
+    exact = closed_forms.laminate_stiffness([tuple(ms.lame[0]), tuple(ms.lame[1])], [0.5, 0.5])
+    H = hom.Homogenization(ms, precision=precision, scheme=scheme)
+    info = H.solve(0, 1e-10 if precision == 0 else 1e-7)
+    assert all(i["status"] == 0 for i in info), info
+    assert rel_err(H.effective(0), exact) < (1e-9 if precision == 0 else 1e-6)
+    H.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_random_spheres_32_cg_vs_oracle(precision):
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.random_spheres((32, 32, 32), seed=3)
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    loads = [0, 3]
+    refs = []
+    for a in loads:
+        e, _, _ = pb.cg(pb.rhs(unit_mandel_load(a)), 1e-12)
+        refs.append(tensor_to_mandel(e))
+    H = hom.Homogenization(ms, precision=precision, scheme=hom.HOM_CG)
+    info = H.solve(0, 1e-12 if precision == 0 else 1e-7)
+    assert all(i["status"] == 0 for i in info), info
+    for r, a in zip(refs, loads):
+        assert rel_err(H.field(0, a), r) < TOL[precision]
+    c = H.effective(0)
+    assert rel_err(c, c.T) < (1e-9 if precision == 0 else 1e-6)
+    H.close()
+
+
+def test_homogeneous_medium_gives_zero_strain():
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(8, matrix=(2.0, 3.0), inclusion=(2.0, 3.0))
+    for prec, scheme in [(0, 0), (1, 1)]:
+        H = hom.Homogenization(ms, precision=prec, scheme=scheme)
+        info = H.solve(0, 1e-8)
+        assert all(i["status"] == 0 for i in info)
+        assert np.abs(H.field(0, 2)).max() < 1e-12
+        expect = np.diag([6.0] * 6) + 2.0 * (np.arange(6)[:, None] < 3) * (np.arange(6)[None] < 3)
+        np.testing.assert_allclose(H.effective(0), expect, atol=1e-10)
+        H.close()
+
+
+def test_custom_loads_are_linear_combinations():
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.Microstructure(random_phase((16, 8, 12), 3, 4), np.array([[1.0, 1.0], [5.0, 2.0], [0.5, 0.4]]),
+                                  2.0, 1.5)
+    H = hom.Homogenization(ms, precision=0)
+    H.solve(0, 1e-12)
+    c = H.effective(0)
+    L = np.random.default_rng(2).standard_normal((4, 6))
+    H.solve(0, 1e-12, loads=L)
+    np.testing.assert_allclose(H.effective(0), c @ L.T, atol=1e-9 * np.abs(c).max())
+    H.close()
+
+
+def test_not_converged_is_reported():
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.random_spheres((16, 16, 16), seed=2)
+    H = hom.Homogenization(ms, precision=0, scheme=hom.HOM_CG, max_iter=3, check_every=1, max_refine=0)
+    info = H.solve(0, 1e-12)
+    assert all(i["status"] == hom.HOM_ERR_NOT_CONVERGED for i in info)
+    assert all(i["iterations"] <= 3 for i in info)
+    H.close()
