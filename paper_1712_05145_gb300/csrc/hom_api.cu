@@ -430,7 +430,10 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
       if (!need) break;
       CKS(write_states(c, st));
       {
-        auto fa = fwd_args<Tf, TR>(c, FWD_TAU, 6, 6);
+        // r = b - A x evaluated as b - Gamma0 * (C : (x + E)): equal to the literal residual on
+        // compatible x and exactly compatible itself, so CG restarts inside the subspace where
+        // A is self-adjoint in the C0 product
+        auto fa = fwd_args<Tf, TR>(c, FWD_STRESS, 6, 6);
         fa.in = x;
         fa.E = dE;
         fa.st = c->d_st;
@@ -439,7 +442,6 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
         auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RESID, 6, 6, 6);
         ia.out = r;
         ia.b = bfield;
-        ia.sub = x;
         ia.st = c->d_st;
         CKS((ls_pass<Tf, TR>(c, n, fa, za, ia, &act)));
       }
@@ -470,7 +472,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
     std::vector<int> act(n, 1);
     for (int i = 0; i < n; ++i) st[i].active = 1;
     CKS(write_states(c, st));
-    auto fa = fwd_args<Tf, TR>(c, FWD_TAU, 6, 6);
+    auto fa = fwd_args<Tf, TR>(c, FWD_STRESS, 6, 6);
     fa.in = x;
     fa.E = dE;
     fa.st = c->d_st;
@@ -479,7 +481,6 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
     auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RESID, 6, 6, 6);
     ia.out = r;
     ia.b = bfield;
-    ia.sub = x;
     ia.st = c->d_st;
     // FIN_RESID overwrites res; keep the Cauchy quantity for the report
     std::vector<RhsState> before = st;

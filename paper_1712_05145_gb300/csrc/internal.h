@@ -38,7 +38,11 @@ struct RhsState {
   int pad_;
 };
 
-enum FwdMode { FWD_TAU = 0, FWD_CG = 1, FWD_COPY = 2 };
+// FWD_TAU: tau = (C - C0) : (in + E)     (polarization, Eq. auxiliary_problem)
+// FWD_STRESS: tau = C : (in + E)         (stress; -Gamma0 * sigma is the equilibrium residual)
+// FWD_CG: p = r + beta p, tau = C : p    (CG direction; A p = Gamma0 * (C : p) on compatible p)
+// FWD_COPY: tau = in                     (plain transform)
+enum FwdMode { FWD_TAU = 0, FWD_CG = 1, FWD_COPY = 2, FWD_STRESS = 3 };
 // Z_GAMMA: forward z FFT, -Gamma0_hat contraction, inverse z FFT (the LS step)
 // Z_FWD / Z_INV: forward / inverse z FFT only; Z_GREEN: contraction only (no FFT)
 // Z_DISP: forward z FFT of a strain, displacement u_hat (3 components), inverse z FFT

@@ -36,15 +36,16 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   const uint8_t* php = a.phase + (long long)z * plane_sz;
   T acc = (T)0;
 
-  if (a.mode == FWD_TAU) {
+  if (a.mode == FWD_TAU || a.mode == FWD_STRESS) {
     const T ec = (a.E != nullptr) ? (T)a.E[rhs * 6 + c] : (T)0;
+    const T* w = (a.mode == FWD_TAU) ? tab : tab + a.n_phase;
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = (long long)row * n1 + 2 * c2;
         Tf v0 = 0, v1 = 0;
         if (a.in != nullptr) ld2<Tf>(a.in + foff + o, v0, v1);
         const uchar2 ph = *reinterpret_cast<const uchar2*>(php + o);
-        pl[row * P + c2] = mk<T>(tab[ph.x] * ((T)v0 + ec), tab[ph.y] * ((T)v1 + ec));
+        pl[row * P + c2] = mk<T>(w[ph.x] * ((T)v0 + ec), w[ph.y] * ((T)v1 + ec));
       }
     }
   } else if (a.mode == FWD_CG) {
@@ -60,8 +61,9 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
         const T q1 = (T)r1 + beta * (T)p1;
         st2<Tf>(a.p + foff + o, (Tf)q0, (Tf)q1);
         const uchar2 ph = *reinterpret_cast<const uchar2*>(php + o);
-        acc += tab[a.n_phase + ph.x] * q0 * q0 + tab[a.n_phase + ph.y] * q1 * q1;
-        pl[row * P + c2] = mk<T>(tab[ph.x] * q0, tab[ph.y] * q1);
+        const T c0 = tab[a.n_phase + ph.x], c1 = tab[a.n_phase + ph.y];
+        acc += c0 * q0 * q0 + c1 * q1 * q1;
+        pl[row * P + c2] = mk<T>(c0 * q0, c1 * q1);
       }
     }
   } else {  // FWD_COPY

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
         st2<Tf>(a.out + o, (Tf)v0, (Tf)v1);
       }
     }
-  } else {  // INV_CG: q = p - eta, x += alpha p, r -= alpha q
+  } else {  // INV_CG: q = A p = Gamma0 * (C : p) = -eta, x += alpha p, r -= alpha q
     const long long foff = ((long long)(rhs * 6 + c) * g.n3 + z) * plane_sz;
     const T alpha = (T)a.st[rhs].alpha;
     const T cw = (c == 0) ? c0h : c0d;
@@ -100,9 +100,8 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
         ld2<Tf>(a.p + o, p0, p1);
         ld2<Tf>(a.x + o, x0, x1);
         ld2<Tf>(a.r + o, r0, r1);
-        const T qa = (T)p0 - e.re, qb = (T)p1 - e.im;
         const T xa = (T)x0 + alpha * (T)p0, xb = (T)x1 + alpha * (T)p1;
-        const T ra = (T)r0 - alpha * qa, rb = (T)r1 - alpha * qb;
+        const T ra = (T)r0 + alpha * e.re, rb = (T)r1 + alpha * e.im;
         st2<Tf>(a.x + o, (Tf)xa, (Tf)xb);
         st2<Tf>(a.r + o, (Tf)ra, (Tf)rb);
         q0 += cw * (ra * ra + rb * rb);
