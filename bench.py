@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the FFT-based homogenization hot path on GB300.
+
+One step = one order-0 CG solve of a 128^3 RVE of random non-overlapping spheres (radii
+4-10 voxels, volume fraction 0.3, contrast 100, nu = 0.3) for all 6 unit load cases at once,
+FP32 fields and FFTs with FP64 reductions and FP64 residual-correction sweeps, to relative
+residual 1e-6, followed by the effective stiffness C_eff (hot-path steps a0-a7 and a9).
+
+metric: voxel-iterations per second (voxels x CG iterations summed over the load cases,
+per second of device time), whole job over all ranks.  Also reported: solves/s with p50 /
+p99 step latency, the dominant kernel's roofline (algorithmic bytes per launch over the
+measured HBM copy bandwidth), the LS step's 48 B/voxel-iteration figure, the end-to-end
+number through the C ABI with host buffers, and the CPU oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iters/s of LS step vs HBM roofline; solves/s + p50/p99 at 1e-6 resid"
+WORKLOAD = "order-0 CG, 128^3 random spheres f=0.3, contrast 100, 6 load cases, FP32 fields + FP64 reductions/refinement, tol 1e-6"
+SEED = 1713  # 1712 + configuration index
+GRID = 128
+TOL = 1e-6
+LS_BYTES_PER_VOXEL_ITER = 48  # FP32: read the 6-component strain once, write it once
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1712_05145_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_digest") != kernel_source_digest():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    return None if ent is None else ent.get("dram_bytes_per_launch_full")
+
+
+def cpu_baseline():
+    """The oracle as it stands: one A-application (one CG iteration's LS step) for one load on the
+    same 128^3 microstructure, single-threaded numpy on this host."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from paper_1712_05145_gb300 import synthetic
+from oracle.lippmann_schwinger import Problem
+from oracle.tensors import unit_mandel_load
+ms = synthetic.random_spheres((%d,)*3, seed=%d)
+pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+b = pb.rhs(unit_mandel_load(0))
+t = time.perf_counter(); pb.apply_A(b); dt = time.perf_counter() - t
+print(json.dumps({"seconds": dt, "voxels": ms.phase.size}))
+""" % (ROOT, GRID, SEED)
+    envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv, timeout=900)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+        return {"value": r["voxels"] / r["seconds"], "unit": "voxel-iters/s", "cores": 1, "kind": "oracle",
+                "sample": "one oracle A-application (LS step) of load E=e11 on the same 128^3 RVE, "
+                          "numpy FP64 single-threaded, %.1f s" % r["seconds"]}
+    except Exception as e:  # report, never fail the bench on the baseline leg
+        return {"value": None, "unit": "voxel-iters/s", "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
+
+
+def reference_arm(args):
+    """The oracle timed as the reference arm: each step one oracle A-application of one load on the
+    64^3 discretisation of the same microstructure (bounded sample), host cores."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from paper_1712_05145_gb300 import synthetic
+    from oracle.lippmann_schwinger import Problem
+    from oracle.tensors import unit_mandel_load
+    n = 64
+    ms = synthetic.random_spheres((n, n, n), seed=SEED)
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    b = pb.rhs(unit_mandel_load(0))
+    for _ in range(args.warmup):
+        pb.apply_A(b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pb.apply_A(b)
+    dt = time.perf_counter() - t0
+    value = ms.phase.size * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "voxel-iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": "oracle LS step of one load on the 64^3 "
+                                                                  "discretisation (numpy FP64)"},
+            "cpu_baseline": {"value": value, "unit": "voxel-iters/s", "cores": 1, "kind": "oracle",
+                             "sample": "one oracle A-application per step, 64^3, one load"},
+            "e2e": {"value": value, "unit": "voxel-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1712_05145_gb300 import build, hom, synthetic
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    n = args.grid
+    ms = synthetic.random_spheres((n, n, n), seed=SEED)
+    M = ms.phase.size
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, scheme=hom.HOM_CG, stream=stream.cuda_stream)
+
+    def step():
+        info = H.solve(0, TOL)
+        c = H.effective(0)
+        return info, c
+
+    for _ in range(max(3, args.warmup)):
+        info, c_eff = step()
+    bad = [i for i in info if i["status"] != 0]
+    if bad:
+        raise RuntimeError("warm-up solve did not converge: %s" % bad)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    hom.hom_profile(H.h, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    iters = 0
+    per_step_iters = []
+    ev[0].record(stream)
+    for k in range(args.steps):
+        info, _ = step()
+        it = sum(i["iterations"] for i in info)
+        iters += it
+        per_step_iters.append(it)
+        ev[k + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    prof = hom.hom_profile_read(H.h)
+    hom.hom_profile(H.h, 0)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    worst = [i["rel_residual_fp64"] for i in info]
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    vi = torch.tensor([float(M) * iters], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(vi, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    value = float(vi.item()) / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: create from host arrays, solve, read C_eff
+    e2e = None
+    if not args.no_e2e:
+        e2e_iters = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps // 2)):
+            opt = hom.hom_default_options()
+            h = hom.hom_create((n, n, n), ms.phase, ms.lame, ms.lam0, ms.mu0, opt)
+            inf = hom.hom_solve(h, 0, TOL)
+            hom.hom_effective(h, 0, 6)
+            hom.hom_destroy(h)
+            e2e_iters += sum(i["iterations"] for i in inf)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": M * e2e_iters / e2e_s * world, "unit": "voxel-iters/s",
+               "h2d_bytes_per_step": int(M + ms.lame.nbytes), "d2h_bytes_per_step": 6 * 6 * 8,
+               "steps": max(1, args.steps // 2),
+               "note": "hom_create from host phase/Lame arrays + hom_solve + hom_effective to host + hom_destroy"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    dom = max(prof, key=lambda p: p["ms"])
+    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9 if dom["ms"] > 0 else 0.0
+    traffic = ncu_traffic(dom["kernel"])
+    launches = {p["kernel"]: p["launches"] for p in prof}
+    ls_ms = sum(p["ms"] for p in prof)
+    # voxel-iterations of the timed region include the FP64 residual sweeps' LS steps
+    ls_voxel_iters = sum(p["voxel_comps"] for p in prof if p["kernel"] == "plane_inv") / 6.0
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "voxel-iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [n, n, n], "loads": 6, "tol": TOL, "seed": SEED,
+                   "l2": "inputs larger than L2 (x, r, p fields 302 MB each)", "parallelism": "replicas"},
+        "solves_per_s": world * args.steps / (total_ms / 1e3),
+        "p50_ms": float(np.percentile(step_ms, 50)),
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "cg_iterations_per_step": per_step_iters,
+        "rel_residual_fp64_max": max(worst),
+        "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "bytes_per_launch": dom["bytes"] / max(1, dom["launches"]),
+                     "launch_ms": dom["ms"] / max(1, dom["launches"])},
+        "ls_step": {"voxel_iters": ls_voxel_iters, "device_ms": ls_ms,
+                    "achieved_gbs_at_48B": LS_BYTES_PER_VOXEL_ITER * ls_voxel_iters / (ls_ms / 1e3) / 1e9,
+                    "frac_of_hbm": LS_BYTES_PER_VOXEL_ITER * ls_voxel_iters / (ls_ms / 1e3) / 1e9 / peak},
+        "kernels": prof,
+        "gpu_launches": int(sum(launches.values())),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    H.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

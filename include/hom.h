@@ -150,6 +150,26 @@ HOM_API hom_status hom_fft_inverse(hom_t h, int32_t nfield, const double* fhat, 
  * tau_hat, eta_hat: device double complex [nrhs][6][N3][N2][N1/2+1] Mandel. */
 HOM_API hom_status hom_green_apply(hom_t h, int32_t nrhs, const double* tau_hat, double* eta_hat);
 
+/* Per-kernel accounting for performance measurement (off by default).
+ * Kernel kinds of the Lippmann-Schwinger step: */
+enum { HOM_KERNEL_PLANE_FWD = 0, HOM_KERNEL_ZPASS = 1, HOM_KERNEL_PLANE_INV = 2, HOM_KERNEL_COUNT = 3 };
+
+typedef struct {
+  int64_t launches;     /* kernel launches */
+  int64_t bytes;        /* algorithmic bytes: every input and output element the working CTAs
+                           must read or write once (fields, phase bytes, spectrum scratch) */
+  int64_t voxel_comps;  /* voxel-component units (plane kernels) or spectrum-column units
+                           (z pass) processed by CTAs that did work */
+  double ms;            /* device time summed over launches (CUDA events on the handle's stream) */
+} hom_kernel_stat;
+
+/* enable != 0 starts accounting (and resets the counters); 0 stops it.  While enabled each
+ * LS-step launch is bracketed by CUDA events and counts its bytes on the device. */
+HOM_API hom_status hom_profile(hom_t h, int32_t enable);
+
+/* Reads the counters into out[HOM_KERNEL_COUNT] (host array); synchronizes the stream. */
+HOM_API hom_status hom_profile_read(hom_t h, hom_kernel_stat* out);
+
 /* Bytes of device memory the handle holds now. */
 HOM_API int64_t hom_device_bytes(hom_t h);
 

@@ -90,6 +90,14 @@ struct hom_ctx {
   size_t bytes = 0;
   std::vector<void*> allocs;
   std::string err;
+  // per-kernel accounting (hom_profile)
+  bool prof_on = false;
+  unsigned long long* d_prof = nullptr;  // [HOM_KERNEL_COUNT][bytes, units]
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[HOM_KERNEL_COUNT] = {0, 0, 0};
+  long long prof_launches[HOM_KERNEL_COUNT] = {0, 0, 0};
 };
 
 namespace {
@@ -204,6 +212,7 @@ FwdArgs<Tf, T> fwd_args(hom_ctx* c, int mode, int ncomp, int in_ncomp) {
   a.n_phase = c->nphase;
   a.part = part_fwd(c);
   a.cnt = cnt_fwd(c);
+  a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_PLANE_FWD : nullptr;
   a.tw_h = tw<T>(c, 0);
   a.tw_n1 = tw<T>(c, 1);
   a.tw_n2 = tw<T>(c, 2);
@@ -219,6 +228,7 @@ ZArgs<T> z_args(hom_ctx* c, int mode, int nin, int nout) {
   a.lam0 = c->lam0;
   a.mu0 = c->mu0;
   a.scale = 1.0 / (double)c->g.M;
+  a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_ZPASS : nullptr;
   a.tw_n3 = tw<T>(c, 3);
   zpass_tiling<T>(a);
   return a;
@@ -236,6 +246,7 @@ InvArgs<Tf, T> inv_args(hom_ctx* c, int mode, int fin, int ncomp, int out_ncomp,
   a.c0d = (T)(2.0 * c->mu0);
   a.part = part_inv(c);
   a.cnt = cnt_inv(c);
+  a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_PLANE_INV : nullptr;
   a.tw_h = tw<T>(c, 0);
   a.tw_n1 = tw<T>(c, 1);
   a.tw_n2 = tw<T>(c, 2);
@@ -256,6 +267,51 @@ template <> cx<double>* spec<double>(hom_ctx* c, int* chunk) {
   return reinterpret_cast<cx<double>*>(c->d_S);
 }
 
+cudaEvent_t pool_event(hom_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Sums the device time of every completed accounted launch (synchronizes the stream).
+hom_status prof_drain(hom_ctx* c) {
+  if (c->pending.empty()) return HOM_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    c->prof_ms[p.kind] += ms;
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  return HOM_OK;
+}
+
+// Launches one LS-step kernel; while accounting is on, brackets it with CUDA events.
+template <typename F>
+hom_status timed_launch(hom_ctx* c, int kind, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->prof_on) {
+    a = pool_event(c);
+    b = pool_event(c);
+    CK(cudaEventRecord(a, c->stream));
+  }
+  CK(launch());
+  if (c->prof_on) {
+    CK(cudaEventRecord(b, c->stream));
+    c->pending.push_back({kind, a, b});
+    c->prof_launches[kind] += 1;
+    if (c->pending.size() > 4096) CKS(prof_drain(c));
+  }
+  return HOM_OK;
+}
+
 // One full LS pass (plane_fwd, zpass, plane_inv) over loads [0, nrhs), chunk by chunk.
 template <typename Tf, typename T>
 hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf, T> fa, ZArgs<T> za, InvArgs<Tf, T> ia,
@@ -273,9 +329,9 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf, T> fa, ZArgs<T> za, InvArgs
     fa.S = S;
     za.S = S;
     ia.S = S;
-    CK(launch_plane_fwd<Tf, T>(fa, n, c->stream));
-    CK(launch_zpass<T>(za, n, c->stream));
-    CK(launch_plane_inv<Tf, T>(ia, n, c->stream));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf, T>(fa, n, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<T>(za, n, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf, T>(ia, n, c->stream); }));
   }
   return HOM_OK;
 }
@@ -305,7 +361,10 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
   Tf* r = reinterpret_cast<Tf*>(vr);
   Tf* p = reinterpret_cast<Tf*>(vp);
   const bool basic = (c->opt.scheme == HOM_BASIC);
-  const double tol_inner = c->fp32 ? 0.5 * tol : tol;
+  // FP32 sweeps are asked for a reduction FP32 can deliver relative to the residual they
+  // start from (kSweepGain); the FP64 residual sweep between them restarts CG exactly.
+  const double kSweepGain = 1e-5;
+  const double tol_inner = c->fp32 ? std::max(0.5 * tol, basic ? 0.0 : kSweepGain) : tol;
 
   std::vector<RhsState> st(n);
   for (int i = 0; i < n; ++i) {
@@ -368,19 +427,19 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
       }
     }
   } else {
-    // r = b - A x with x = 0, in FP64 FFTs
+    // r = b with x = 0 (FFTs in the field precision; the FP64 sweeps recompute b exactly)
     CK(cudaMemsetAsync(x, 0, fb, c->stream));
     {
-      auto fa = fwd_args<Tf, TR>(c, FWD_TAU, 6, 6);
+      auto fa = fwd_args<Tf, T>(c, FWD_TAU, 6, 6);
       fa.E = dE;
       fa.st = c->d_st;
-      auto za = z_args<TR>(c, Z_GAMMA, 6, 6);
+      auto za = z_args<T>(c, Z_GAMMA, 6, 6);
       za.st = c->d_st;
-      auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RHS, 6, 6, 6);
+      auto ia = inv_args<Tf, T>(c, INV_STORE, FIN_RHS, 6, 6, 6);
       ia.out = r;
       ia.b = bfield;
       ia.st = c->d_st;
-      CKS((ls_pass<Tf, TR>(c, n, fa, za, ia)));
+      CKS((ls_pass<Tf, T>(c, n, fa, za, ia)));
     }
     CKS(read_states(c, n, st));
     std::vector<int> act(n, 1);
@@ -455,6 +514,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
         } else if (refine[i] < c->opt.max_refine && st[i].iter < st[i].max_iter) {
           refine[i] += 1;
           st[i].active = 1;  // restart CG from the FP64 residual
+          st[i].tol = c->fp32 ? std::max(0.5 * tol, kSweepGain * st[i].res_true) : 0.5 * tol;
           again = true;
         } else {
           st[i].active = 0;
@@ -572,16 +632,16 @@ hom_status displacements(hom_ctx* c, int order) {
     fa.in = reinterpret_cast<const Tf*>(o.eps);
     fa.rhs0 = r0;
     fa.S = S;
-    CK((launch_plane_fwd<Tf, Tf>(fa, m, c->stream)));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf, Tf>(fa, m, c->stream); }));
     auto za = z_args<Tf>(c, Z_DISP, 6, 3);
     za.S = S;
     za.rhs0 = r0;
-    CK(launch_zpass<Tf>(za, m, c->stream));
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<Tf>(za, m, c->stream); }));
     auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 3, 3, 6);
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = reinterpret_cast<Tf*>(o.disp);
-    CK((launch_plane_inv<Tf, Tf>(ia, m, c->stream)));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf, Tf>(ia, m, c->stream); }));
   }
   return HOM_OK;
 }
@@ -610,16 +670,16 @@ hom_status build_rhs(hom_ctx* c, int order, Tf* b, Tf* pf) {
     fa.in = f9;
     fa.rhs0 = r0;
     fa.S = S;
-    CK((launch_plane_fwd<Tf, Tf>(fa, m, c->stream)));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf, Tf>(fa, m, c->stream); }));
     auto za = z_args<Tf>(c, Z_RHS, 9, 6);
     za.S = S;
     za.rhs0 = r0;
-    CK(launch_zpass<Tf>(za, m, c->stream));
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<Tf>(za, m, c->stream); }));
     auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 6, 6, 9);
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = b;
-    CK((launch_plane_inv<Tf, Tf>(ia, m, c->stream)));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf, Tf>(ia, m, c->stream); }));
   }
   return HOM_OK;
 }
@@ -745,9 +805,46 @@ HOM_API const char* hom_last_error(hom_t h) { return h ? h->err.c_str() : "null 
 
 HOM_API int64_t hom_device_bytes(hom_t h) { return h ? (int64_t)h->bytes : 0; }
 
+HOM_API hom_status hom_profile(hom_t c, int32_t enable) {
+  if (!c) return HOM_ERR_ARG;
+  CKS(prof_drain(c));
+  if (enable) {
+    if (!c->d_prof) CKS(dalloc(c, (void**)&c->d_prof, sizeof(unsigned long long) * 2 * HOM_KERNEL_COUNT));
+    CK(cudaMemsetAsync(c->d_prof, 0, sizeof(unsigned long long) * 2 * HOM_KERNEL_COUNT, c->stream));
+    for (int k = 0; k < HOM_KERNEL_COUNT; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_launches[k] = 0;
+    }
+  }
+  c->prof_on = (enable != 0);
+  return HOM_OK;
+}
+
+HOM_API hom_status hom_profile_read(hom_t c, hom_kernel_stat* out) {
+  if (!c || !out) return HOM_ERR_ARG;
+  CKS(prof_drain(c));
+  unsigned long long hp[2 * HOM_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  if (c->d_prof) {
+    CK(cudaMemcpyAsync(hp, c->d_prof, sizeof(hp), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  for (int k = 0; k < HOM_KERNEL_COUNT; ++k) {
+    out[k].launches = c->prof_launches[k];
+    out[k].bytes = (int64_t)hp[2 * k];
+    out[k].voxel_comps = (int64_t)hp[2 * k + 1];
+    out[k].ms = c->prof_ms[k];
+  }
+  return HOM_OK;
+}
+
 HOM_API void hom_destroy(hom_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;

@@ -67,6 +67,7 @@ struct FwdArgs {
   RhsState* st;                // nullable
   double* part;                // [rhs][2][ncta] partial sums
   unsigned* cnt;               // [rhs] tickets
+  unsigned long long* prof;    // nullable: [bytes, units] of this kernel kind
   const cx<T>* tw_h;
   const cx<T>* tw_n1;
   const cx<T>* tw_n2;
@@ -84,6 +85,7 @@ struct ZArgs {
   const RhsState* st;
   double lam0, mu0;
   double scale;          // factor applied with the spectral operator (1/M after a forward FFT)
+  unsigned long long* prof;
   const cx<T>* tw_n3;
 };
 
@@ -105,6 +107,7 @@ struct InvArgs {
   RhsState* st;
   double* part;
   unsigned* cnt;
+  unsigned long long* prof;
   const cx<T>* tw_h;
   const cx<T>* tw_n1;
   const cx<T>* tw_n2;

@@ -33,6 +33,14 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
 
   const long long plane_sz = (long long)n2 * n1;
   const long long foff = ((long long)(rhs * a.in_ncomp + c) * g.n3 + z) * plane_sz;
+  if (a.prof != nullptr && tid == 0) {
+    // algorithmic bytes: field planes read/written once, phase bytes, spectrum plane written
+    long long fields = (a.mode == FWD_CG) ? 3 : ((a.mode == FWD_COPY || a.in != nullptr) ? 1 : 0);
+    long long b = fields * plane_sz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>);
+    if (a.mode != FWD_COPY) b += plane_sz;
+    atomicAdd(a.prof, (unsigned long long)b);
+    atomicAdd(a.prof + 1, (unsigned long long)plane_sz);
+  }
   const uint8_t* php = a.phase + (long long)z * plane_sz;
   T acc = (T)0;
 

@@ -22,6 +22,12 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
 
   const cx<T>* Sp = a.S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
+  if (a.prof != nullptr && tid == 0) {
+    const long long psz = (long long)n2 * n1;
+    long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.b != nullptr) + (a.sub != nullptr) + (a.fin == FIN_BASIC);
+    atomicAdd(a.prof, (unsigned long long)(fields * psz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>)));
+    atomicAdd(a.prof + 1, (unsigned long long)psz);
+  }
   const long long nmain = (long long)n2 * h;
   for (int row = warp; row < n2; row += nwarp) {
     for (int col = lane; col < h; col += 32) {

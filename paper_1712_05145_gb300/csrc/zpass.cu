@@ -76,6 +76,11 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
   const int cstride = n3 * TC;
   const int tid = threadIdx.x, nthr = blockDim.x;
   cx<T>* Sr = a.S + (long long)lrhs * a.ncomp_in * n3 * g.plane_c;
+  if (a.prof != nullptr && tid == 0) {
+    const long long cols = (g.plane_c - f0 < TC) ? g.plane_c - f0 : TC;
+    atomicAdd(a.prof, (unsigned long long)((a.ncomp_in + a.ncomp_out) * n3 * cols * (long long)sizeof(cx<T>)));
+    atomicAdd(a.prof + 1, (unsigned long long)(n3 * cols));
+  }
 
   for (int e = tid; e < a.ncomp_in * n3 * TC; e += nthr) {
     const int tc = e & (TC - 1), row = e >> tc_log2;

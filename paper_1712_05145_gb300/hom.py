@@ -33,9 +33,15 @@ HOM_FIELD_STRAIN = 0
 HOM_FIELD_DISPLACEMENT = 1
 HOM_FIELD_STRESS = 2
 
+HOM_KERNEL_PLANE_FWD = 0
+HOM_KERNEL_ZPASS = 1
+HOM_KERNEL_PLANE_INV = 2
+HOM_KERNEL_COUNT = 3
+KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv"]
+
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
-            "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply",
-            "hom_device_bytes", "hom_last_error", "hom_status_string", "hom_destroy"]
+            "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
+            "hom_profile_read", "hom_device_bytes", "hom_last_error", "hom_status_string", "hom_destroy"]
 
 
 class hom_options(ctypes.Structure):
@@ -53,6 +59,11 @@ class hom_solve_info(ctypes.Structure):
     def as_dict(self):
         return {"iterations": self.iterations, "refinements": self.refinements, "status": self.status,
                 "rel_residual": self.rel_residual, "rel_residual_fp64": self.rel_residual_fp64}
+
+
+class hom_kernel_stat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("bytes", ctypes.c_int64), ("voxel_comps", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
 
 
 class HomError(RuntimeError):
@@ -93,6 +104,10 @@ def load_library(path=None):
     lib.hom_fft_inverse.restype = I32
     lib.hom_green_apply.argtypes = [V, I32, V, V]
     lib.hom_green_apply.restype = I32
+    lib.hom_profile.argtypes = [V, I32]
+    lib.hom_profile.restype = I32
+    lib.hom_profile_read.argtypes = [V, V]
+    lib.hom_profile_read.restype = I32
     lib.hom_device_bytes.argtypes = [V]
     lib.hom_device_bytes.restype = I64
     lib.hom_last_error.argtypes = [V]
@@ -195,6 +210,18 @@ def hom_fft_inverse(h, nfield, fhat, f):
 def hom_green_apply(h, nrhs, tau_hat, eta_hat):
     _check(h, load_library().hom_green_apply(h, int(nrhs), _ptr(tau_hat), _ptr(eta_hat)))
     return eta_hat
+
+
+def hom_profile(h, enable):
+    _check(h, load_library().hom_profile(h, int(bool(enable))))
+
+
+def hom_profile_read(h):
+    """Per-kernel counters: list of dicts (launches, bytes, voxel_comps, ms) by kernel kind."""
+    out = (hom_kernel_stat * HOM_KERNEL_COUNT)()
+    _check(h, load_library().hom_profile_read(h, ctypes.cast(out, ctypes.c_void_p)))
+    return [{"kernel": KERNEL_NAMES[k], "launches": out[k].launches, "bytes": out[k].bytes,
+             "voxel_comps": out[k].voxel_comps, "ms": out[k].ms} for k in range(HOM_KERNEL_COUNT)]
 
 
 def hom_device_bytes(h):
