@@ -78,6 +78,16 @@ cudaError_t launch_convert(const Ti* in, To* out, long long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// x += d (FP64 solution updated by an FP32 correction)
+__global__ void add_correction_kernel(const float* __restrict__ d, double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+cudaError_t launch_add_correction(const float* d, double* x, long long n, cudaStream_t s) {
+  add_correction_kernel<<<grid_for(n, 256), 256, 0, s>>>(d, x, n);
+  return cudaGetLastError();
+}
+
 // ---- spectrum layouts ------------------------------------------------------------
 // internal: per plane, n2 rows of h values (kx < n1/2) then the n2 Nyquist values;
 // standard: [n3][n2][n1/2 + 1] complex.  basis: 0 keep, 1 Mandel->Kelvin, 2 Kelvin->Mandel

@@ -74,8 +74,9 @@ struct hom_ctx {
   size_t S_rhs_bytes = 0;
   int chunk = 1;
   int S_comps = 6;      // component planes d_S holds (per z-plane set)
-  cx<double>* d_S64 = nullptr;  // FP64 spectrum for residual sweeps (FP32 mode)
+  cx<double>* d_S64 = nullptr;  // FP64 spectrum for residual sweeps and RHS builds (FP32 mode)
   int chunk64 = 1;
+  int S64_comps = 6;
   int cap = 0;  // loads the state / partial arrays hold
   RhsState* d_st = nullptr;
   double* d_part = nullptr;  // [2][cap][2][6*n3]
@@ -84,8 +85,8 @@ struct hom_ctx {
   double* d_mpart = nullptr; // mean reduction partials
   double* d_mout = nullptr;
   int mblk = 64;
-  void* d_work[3] = {nullptr, nullptr, nullptr};
-  size_t work_bytes[3] = {0, 0, 0};
+  void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t work_bytes[4] = {0, 0, 0, 0};
   OrderData ord[3];
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -312,9 +313,11 @@ hom_status timed_launch(hom_ctx* c, int kind, F&& launch) {
   return HOM_OK;
 }
 
-// One full LS pass (plane_fwd, zpass, plane_inv) over loads [0, nrhs), chunk by chunk.
-template <typename Tf, typename T>
-hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf, T> fa, ZArgs<T> za, InvArgs<Tf, T> ia,
+// One full LS pass (plane_fwd, zpass, plane_inv) over loads [0, nrhs), chunk by chunk.  The
+// forward kernel reads fields of type Tf1, the inverse kernel writes fields of type Tf3, and the
+// transforms run in T.
+template <typename Tf1, typename Tf3, typename T>
+hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArgs<Tf3, T> ia,
                    const std::vector<int>* active = nullptr) {
   int chunk;
   cx<T>* S = spec<T>(c, &chunk);
@@ -329,9 +332,9 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf, T> fa, ZArgs<T> za, InvArgs
     fa.S = S;
     za.S = S;
     ia.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf, T>(fa, n, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf1, T>(fa, n, c->stream); }));
     CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<T>(za, n, c->stream); }));
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf, T>(ia, n, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf3, T>(ia, n, c->stream); }));
   }
   return HOM_OK;
 }
@@ -347,24 +350,53 @@ hom_status write_states(hom_ctx* c, const std::vector<RhsState>& h) {
   return HOM_OK;
 }
 
-// Solves A x = b (Eq. cg_form) for n loads.  b = -Gamma0 * (C : E) for Kelvin loads dE
-// (order 0, dE device [n][6]) or b = bfield (higher orders).  x receives the solution.
-template <typename Tf, typename T>
-hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, Tf* x, double tol,
+template <typename Tf>
+size_t tbytes(const hom_ctx* c, int nf, int ncomp) {
+  return (size_t)nf * ncomp * (size_t)c->g.M * sizeof(Tf);
+}
+
+// FP64 residual sweep r = b - A x, evaluated as b - Gamma0 * (C : (x + E)) (Eq. cg_form with
+// A = Gamma0 * C on compatible fields): equal to the literal residual on compatible x, and
+// itself exactly compatible, so CG restarts inside the subspace where A is self-adjoint in the
+// C0 product.  x and b are FP64; r is written in the iteration precision Tf.
+template <typename Tf>
+hom_status residual_sweep(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
+                          int fin, const std::vector<int>* act) {
+  auto fa = fwd_args<double, double>(c, FWD_STRESS, 6, 6);
+  fa.in = x64;
+  fa.E = dE;
+  fa.st = c->d_st;
+  auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+  za.st = c->d_st;
+  auto ia = inv_args<Tf, double>(c, INV_STORE, fin, 6, 6, 6);
+  ia.out = r;
+  ia.b = b64;
+  ia.st = c->d_st;
+  return ls_pass<double, Tf, double>(c, n, fa, za, ia, act);
+}
+
+// Solves A x = b (Eq. cg_form) for n loads; b = -Gamma0 * (C : E) for Kelvin loads dE (order 0,
+// device [n][6]) or b = b64 (higher orders).  The solution x64 is FP64 in both precisions.
+//  FP64 mode (Tf = double): Basic Scheme or CG in FP64 directly on x64.
+//  FP32 mode (Tf = float): iterative refinement -- each sweep runs FP32 CG on A d = r from d = 0
+//  (FP64 reductions), then x64 += d and an FP64 residual sweep restarts the next one.
+template <typename Tf>
+hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, double* x64, double tol,
                         hom_solve_info* info) {
-  using TR = double;  // residual sweeps always run the FFTs in FP64
+  const bool mixed = sizeof(Tf) == sizeof(float);
   CKS(ensure_cap(c, n));
-  const size_t fb = field_bytes(c, n, 6);
-  void *vr, *vp;
+  const size_t fb = tbytes<Tf>(c, n, 6);
+  void *vr, *vp, *vd = nullptr;
   CKS(work(c, 0, fb, &vr));
   CKS(work(c, 1, fb, &vp));
+  if (mixed) CKS(work(c, 3, fb, &vd));
   Tf* r = reinterpret_cast<Tf*>(vr);
   Tf* p = reinterpret_cast<Tf*>(vp);
+  Tf* d = mixed ? reinterpret_cast<Tf*>(vd) : reinterpret_cast<Tf*>(x64);
   const bool basic = (c->opt.scheme == HOM_BASIC);
-  // FP32 sweeps are asked for a reduction FP32 can deliver relative to the residual they
-  // start from (kSweepGain); the FP64 residual sweep between them restarts CG exactly.
+  // an FP32 sweep is asked for a reduction FP32 can deliver relative to its starting residual
   const double kSweepGain = 1e-5;
-  const double tol_inner = c->fp32 ? std::max(0.5 * tol, basic ? 0.0 : kSweepGain) : tol;
+  const double tol_inner = (mixed && !basic) ? std::max(0.5 * tol, kSweepGain) : (mixed ? 0.5 * tol : tol);
 
   std::vector<RhsState> st(n);
   for (int i = 0; i < n; ++i) {
@@ -376,39 +408,38 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
     st[i] = s;
   }
   CKS(write_states(c, st));
-  std::vector<int> refine(n, 0), done(n, 0);
+  std::vector<int> refine(n, 0), done(n, 0), act(n, 1);
 
   if (basic) {
-    // eps_0 = b (Algorithm 1 INIT), then eps_{k+1} = b + T(eps_k) = T(eps_k + E) [+ b field]
-    Tf* buf[2] = {x, p};
+    // eps_0 = b (Algorithm 1 INIT); eps_{k+1} = b + T(eps_k), here T(eps_k + E) (+ b field)
+    Tf* buf[2] = {d, p};
     {
-      auto fa = fwd_args<Tf, T>(c, FWD_TAU, 6, 6);
+      auto fa = fwd_args<Tf, Tf>(c, FWD_TAU, 6, 6);
       fa.E = dE;
       fa.st = c->d_st;
-      auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+      auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
       za.st = c->d_st;
-      auto ia = inv_args<Tf, T>(c, INV_STORE, FIN_RHS, 6, 6, 6);
+      auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_RHS, 6, 6, 6);
       ia.out = buf[0];
-      ia.b = bfield;
+      ia.b = b64;
       ia.st = c->d_st;
-      CKS((ls_pass<Tf, T>(c, n, fa, za, ia)));
+      CKS((ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia)));
     }
     int it = 0;
-    std::vector<int> act(n, 1);
     while (true) {
       for (int k = 0; k < c->opt.check_every; ++k, ++it) {
-        auto fa = fwd_args<Tf, T>(c, FWD_TAU, 6, 6);
+        auto fa = fwd_args<Tf, Tf>(c, FWD_TAU, 6, 6);
         fa.in = buf[it & 1];
         fa.E = dE;
         fa.st = c->d_st;
-        auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+        auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
         za.st = c->d_st;
-        auto ia = inv_args<Tf, T>(c, INV_STORE, FIN_BASIC, 6, 6, 6);
+        auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_BASIC, 6, 6, 6);
         ia.out = buf[(it + 1) & 1];
         ia.prev = buf[it & 1];
-        ia.b = bfield;
+        ia.b = b64;
         ia.st = c->d_st;
-        CKS((ls_pass<Tf, T>(c, n, fa, za, ia, &act)));
+        CKS((ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia, &act)));
       }
       CKS(read_states(c, n, st));
       bool any = false;
@@ -418,58 +449,73 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
       }
       if (!any) break;
     }
-    // the result of load i sits in buf[iter_i & 1]
+    // the iterate of load i sits in buf[iter_i & 1]
+    const size_t one = tbytes<Tf>(c, 1, 6);
     for (int i = 0; i < n; ++i) {
-      if (st[i].iter & 1) {
-        const size_t one = field_bytes(c, 1, 6);
-        CK(cudaMemcpyAsync(reinterpret_cast<char*>(buf[0]) + one * i, reinterpret_cast<char*>(buf[1]) + one * i,
-                           one, cudaMemcpyDeviceToDevice, c->stream));
+      const Tf* src = reinterpret_cast<const Tf*>(reinterpret_cast<const char*>(buf[st[i].iter & 1]) + one * i);
+      if (mixed) {
+        CK((launch_convert<Tf, double>(src, x64 + (size_t)i * 6 * c->g.M, 6 * c->g.M, c->stream)));
+      } else if (st[i].iter & 1) {
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(x64) + one * i, src, one, cudaMemcpyDeviceToDevice, c->stream));
       }
     }
+    // report the FP64 residual of the fixed point (the Cauchy quantity stays in `res`)
+    std::vector<RhsState> before = st;
+    for (int i = 0; i < n; ++i) st[i].active = 1;
+    CKS(write_states(c, st));
+    std::vector<int> all(n, 1);
+    CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &all));
+    CKS(read_states(c, n, st));
+    for (int i = 0; i < n; ++i) {
+      st[i].res = before[i].res;
+      st[i].status = before[i].status;
+      done[i] = (before[i].status == 0);
+    }
   } else {
-    // r = b with x = 0 (FFTs in the field precision; the FP64 sweeps recompute b exactly)
-    CK(cudaMemsetAsync(x, 0, fb, c->stream));
-    {
-      auto fa = fwd_args<Tf, T>(c, FWD_TAU, 6, 6);
+    CK(cudaMemsetAsync(x64, 0, tbytes<double>(c, n, 6), c->stream));
+    if (mixed) CK(cudaMemsetAsync(d, 0, fb, c->stream));
+    // initial residual r = b (x = 0)
+    if (dE != nullptr) {
+      auto fa = fwd_args<Tf, Tf>(c, FWD_TAU, 6, 6);
       fa.E = dE;
       fa.st = c->d_st;
-      auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+      auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
       za.st = c->d_st;
-      auto ia = inv_args<Tf, T>(c, INV_STORE, FIN_RHS, 6, 6, 6);
+      auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_RHS, 6, 6, 6);
       ia.out = r;
-      ia.b = bfield;
       ia.st = c->d_st;
-      CKS((ls_pass<Tf, T>(c, n, fa, za, ia)));
+      CKS((ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia)));
+    } else {
+      CKS(residual_sweep<Tf>(c, n, nullptr, b64, x64, r, FIN_RHS, nullptr));
     }
     CKS(read_states(c, n, st));
-    std::vector<int> act(n, 1);
     for (int i = 0; i < n; ++i) {
       if (st[i].b2 == 0.0) {  // b = 0: x = 0 is exact
         done[i] = 1;
         act[i] = 0;
         st[i].active = 0;
         st[i].res_true = 0.0;
+        st[i].res = 0.0;
       }
     }
     CKS(write_states(c, st));
     while (true) {
-      // inner CG
       bool any = false;
       for (int i = 0; i < n; ++i) any = any || act[i];
       while (any) {
         for (int k = 0; k < c->opt.check_every; ++k) {
-          auto fa = fwd_args<Tf, T>(c, FWD_CG, 6, 6);
+          auto fa = fwd_args<Tf, Tf>(c, FWD_CG, 6, 6);
           fa.r = r;
           fa.p = p;
           fa.st = c->d_st;
-          auto za = z_args<T>(c, Z_GAMMA, 6, 6);
+          auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
           za.st = c->d_st;
-          auto ia = inv_args<Tf, T>(c, INV_CG, FIN_CG, 6, 6, 6);
+          auto ia = inv_args<Tf, Tf>(c, INV_CG, FIN_CG, 6, 6, 6);
           ia.p = p;
-          ia.x = x;
+          ia.x = d;
           ia.r = r;
           ia.st = c->d_st;
-          CKS((ls_pass<Tf, T>(c, n, fa, za, ia, &act)));
+          CKS((ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia, &act)));
         }
         CKS(read_states(c, n, st));
         any = false;
@@ -478,7 +524,10 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
           any = any || act[i];
         }
       }
-      // FP64 residual sweep r = b - A x for loads not yet finished
+      if (mixed) {  // x += d, d = 0
+        CK(launch_add_correction(reinterpret_cast<const float*>(d), x64, (long long)n * 6 * c->g.M, c->stream));
+        CK(cudaMemsetAsync(d, 0, fb, c->stream));
+      }
       bool need = false;
       for (int i = 0; i < n; ++i) {
         const bool run = !done[i] && st[i].status == 0;
@@ -488,22 +537,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
       }
       if (!need) break;
       CKS(write_states(c, st));
-      {
-        // r = b - A x evaluated as b - Gamma0 * (C : (x + E)): equal to the literal residual on
-        // compatible x and exactly compatible itself, so CG restarts inside the subspace where
-        // A is self-adjoint in the C0 product
-        auto fa = fwd_args<Tf, TR>(c, FWD_STRESS, 6, 6);
-        fa.in = x;
-        fa.E = dE;
-        fa.st = c->d_st;
-        auto za = z_args<TR>(c, Z_GAMMA, 6, 6);
-        za.st = c->d_st;
-        auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RESID, 6, 6, 6);
-        ia.out = r;
-        ia.b = bfield;
-        ia.st = c->d_st;
-        CKS((ls_pass<Tf, TR>(c, n, fa, za, ia, &act)));
-      }
+      CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       CKS(read_states(c, n, st));
       bool again = false;
       for (int i = 0; i < n; ++i) {
@@ -514,7 +548,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
         } else if (refine[i] < c->opt.max_refine && st[i].iter < st[i].max_iter) {
           refine[i] += 1;
           st[i].active = 1;  // restart CG from the FP64 residual
-          st[i].tol = c->fp32 ? std::max(0.5 * tol, kSweepGain * st[i].res_true) : 0.5 * tol;
+          st[i].tol = mixed ? std::max(0.5 * tol, kSweepGain * st[i].res_true) : 0.5 * tol;
           again = true;
         } else {
           st[i].active = 0;
@@ -527,36 +561,11 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
     }
   }
 
-  if (basic) {
-    // report the FP64 residual of the fixed point
-    std::vector<int> act(n, 1);
-    for (int i = 0; i < n; ++i) st[i].active = 1;
-    CKS(write_states(c, st));
-    auto fa = fwd_args<Tf, TR>(c, FWD_STRESS, 6, 6);
-    fa.in = x;
-    fa.E = dE;
-    fa.st = c->d_st;
-    auto za = z_args<TR>(c, Z_GAMMA, 6, 6);
-    za.st = c->d_st;
-    auto ia = inv_args<Tf, TR>(c, INV_STORE, FIN_RESID, 6, 6, 6);
-    ia.out = r;
-    ia.b = bfield;
-    ia.st = c->d_st;
-    // FIN_RESID overwrites res; keep the Cauchy quantity for the report
-    std::vector<RhsState> before = st;
-    CKS((ls_pass<Tf, TR>(c, n, fa, za, ia, &act)));
-    CKS(read_states(c, n, st));
-    for (int i = 0; i < n; ++i) {
-      st[i].res = before[i].res;
-      st[i].status = before[i].status;
-    }
-  }
-
   hom_status worst = HOM_OK;
   for (int i = 0; i < n; ++i) {
     hom_status si = HOM_OK;
     if (st[i].status == 2) si = HOM_ERR_NUMERIC;
-    else if (st[i].status == 1 || (!basic && !done[i]) || (basic && st[i].res_true >= tol && st[i].res >= tol))
+    else if (st[i].status == 1 || !done[i] || (basic && st[i].res_true >= tol && st[i].res >= tol))
       si = HOM_ERR_NOT_CONVERGED;
     if (info) {
       info[i].iterations = st[i].iter;
@@ -577,32 +586,31 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const Tf* bfield, T
 hom_status alloc_order(hom_ctx* c, int order, int nloads, bool with_p) {
   OrderData& o = c->ord[order];
   if (o.eps && o.nloads == nloads) return HOM_OK;
-  if (o.eps) dfree(c, o.eps, field_bytes(c, o.nloads, 6));
-  if (o.disp) dfree(c, o.disp, field_bytes(c, o.nloads, 3));
-  if (o.pf) dfree(c, o.pf, field_bytes(c, o.nloads, 6));
+  if (o.eps) dfree(c, o.eps, tbytes<double>(c, o.nloads, 6));
+  if (o.disp) dfree(c, o.disp, tbytes<double>(c, o.nloads, 3));
+  if (o.pf) dfree(c, o.pf, tbytes<double>(c, o.nloads, 6));
   o.eps = o.disp = o.pf = nullptr;
   o.nloads = nloads;
-  CKS(dalloc(c, &o.eps, field_bytes(c, nloads, 6)));
-  CKS(dalloc(c, &o.disp, field_bytes(c, nloads, 3)));
-  if (with_p) CKS(dalloc(c, &o.pf, field_bytes(c, nloads, 6)));
+  CKS(dalloc(c, &o.eps, tbytes<double>(c, nloads, 6)));
+  CKS(dalloc(c, &o.disp, tbytes<double>(c, nloads, 3)));
+  if (with_p) CKS(dalloc(c, &o.pf, tbytes<double>(c, nloads, 6)));
   return HOM_OK;
 }
 
 // mean stress <C : (eps + E)> (order 0) or <C : eps + p> (higher orders), Mandel [6][n]
-template <typename Tf>
 hom_status mean_stress(hom_ctx* c, int order, std::vector<double>& eff) {
   OrderData& o = c->ord[order];
   const int n = o.nloads;
   CKS(ensure_cap(c, n));
   std::vector<double> hk(n * 6), hp(n * 6, 0.0);
-  if (order == 0) CK(cudaMemcpyAsync(c->d_E, o.loadsK.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice,
-                                     c->stream));
-  CK(launch_weighted_mean<Tf>(reinterpret_cast<const Tf*>(o.eps), 6, n, order == 0 ? c->d_E : nullptr,
-                              c->d_phase, c->d_mat64, 2, c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
+  if (order == 0)
+    CK(cudaMemcpyAsync(c->d_E, o.loadsK.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_weighted_mean<double>(reinterpret_cast<const double*>(o.eps), 6, n, order == 0 ? c->d_E : nullptr,
+                                  c->d_phase, c->d_mat64, 2, c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
   CK(cudaMemcpyAsync(hk.data(), c->d_mout, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
   if (order > 0) {
-    CK(launch_weighted_mean<Tf>(reinterpret_cast<const Tf*>(o.pf), 6, n, nullptr, c->d_phase, c->d_mat64, -1,
-                                c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
+    CK(launch_weighted_mean<double>(reinterpret_cast<const double*>(o.pf), 6, n, nullptr, c->d_phase, c->d_mat64,
+                                    -1, c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
     CK(cudaMemcpyAsync(hp.data(), c->d_mout, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -616,93 +624,91 @@ hom_status mean_stress(hom_ctx* c, int order, std::vector<double>& eff) {
   return HOM_OK;
 }
 
-// Displacement correctors u (e_y(u) = eps, zero mean) of every load of `order`:
+// Displacement correctors u (e_y(u) = eps, zero mean) of every load of `order`, in FP64:
 // forward FFT of the strain, u_hat = -i (2 eps_hat xi - xi (xi . eps_hat xi)/|xi|^2)/|xi|^2,
 // inverse FFT of the 3 components.
-template <typename Tf>
 hom_status displacements(hom_ctx* c, int order) {
   OrderData& o = c->ord[order];
   const int n = o.nloads;
   int chunk;
-  cx<Tf>* S = spec<Tf>(c, &chunk);
-  chunk = c->S_comps / 6;
+  cx<double>* S = spec<double>(c, &chunk);
+  chunk = std::max(1, (c->fp32 ? c->S64_comps : c->S_comps) / 6);
   for (int r0 = 0; r0 < n; r0 += chunk) {
     const int m = std::min(chunk, n - r0);
-    auto fa = fwd_args<Tf, Tf>(c, FWD_COPY, 6, 6);
-    fa.in = reinterpret_cast<const Tf*>(o.eps);
+    auto fa = fwd_args<double, double>(c, FWD_COPY, 6, 6);
+    fa.in = reinterpret_cast<const double*>(o.eps);
     fa.rhs0 = r0;
     fa.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf, Tf>(fa, m, c->stream); }));
-    auto za = z_args<Tf>(c, Z_DISP, 6, 3);
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
+    auto za = z_args<double>(c, Z_DISP, 6, 3);
     za.S = S;
     za.rhs0 = r0;
-    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<Tf>(za, m, c->stream); }));
-    auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 3, 3, 6);
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<double>(za, m, c->stream); }));
+    auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 3, 3, 6);
     ia.S = S;
     ia.rhs0 = r0;
-    ia.out = reinterpret_cast<Tf*>(o.disp);
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf, Tf>(ia, m, c->stream); }));
+    ia.out = reinterpret_cast<double*>(o.disp);
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
   }
   return HOM_OK;
 }
 
 // Right-hand sides b = -Gamma0 * (p_alpha + theta_alpha) of order 1 or 2 (Sec. 3, modified
-// initialization), with p_alpha kept in pf for the effective tensor.
-template <typename Tf>
-hom_status build_rhs(hom_ctx* c, int order, Tf* b, Tf* pf) {
+// initialization), in FP64, with p_alpha kept in pf for the effective tensor.
+hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf) {
   const int n = (order == 1) ? 18 : 36;
   const OrderData& lo = c->ord[order - 1];
   void* v9;
-  CKS(work(c, 0, field_bytes(c, n, 9), &v9));
-  Tf* f9 = reinterpret_cast<Tf*>(v9);
+  CKS(work(c, 3, tbytes<double>(c, n, 9), &v9));
+  double* f9 = reinterpret_cast<double*>(v9);
   CKS(ensure_cap(c, std::max(n, 6)));
   if (order == 1)
     CK(cudaMemcpyAsync(c->d_E, c->ord[0].loadsK.data(), sizeof(double) * 36, cudaMemcpyHostToDevice, c->stream));
-  CK(launch_rhs_pointwise<Tf>(order, n, reinterpret_cast<const Tf*>(lo.disp), reinterpret_cast<const Tf*>(lo.eps),
-                              order == 2 ? reinterpret_cast<const Tf*>(lo.pf) : nullptr, c->d_E, c->d_phase,
-                              c->d_mat64, c->g.M, f9, pf, c->stream));
+  CK(launch_rhs_pointwise<double>(order, n, reinterpret_cast<const double*>(lo.disp),
+                                  reinterpret_cast<const double*>(lo.eps),
+                                  order == 2 ? reinterpret_cast<const double*>(lo.pf) : nullptr, c->d_E, c->d_phase,
+                                  c->d_mat64, c->g.M, f9, pf, c->stream));
   int chunk;
-  cx<Tf>* S = spec<Tf>(c, &chunk);
-  chunk = std::max(1, c->S_comps / 9);
+  cx<double>* S = spec<double>(c, &chunk);
+  chunk = std::max(1, (c->fp32 ? c->S64_comps : c->S_comps) / 9);
   for (int r0 = 0; r0 < n; r0 += chunk) {
     const int m = std::min(chunk, n - r0);
-    auto fa = fwd_args<Tf, Tf>(c, FWD_COPY, 9, 9);
+    auto fa = fwd_args<double, double>(c, FWD_COPY, 9, 9);
     fa.in = f9;
     fa.rhs0 = r0;
     fa.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf, Tf>(fa, m, c->stream); }));
-    auto za = z_args<Tf>(c, Z_RHS, 9, 6);
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
+    auto za = z_args<double>(c, Z_RHS, 9, 6);
     za.S = S;
     za.rhs0 = r0;
-    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<Tf>(za, m, c->stream); }));
-    auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 6, 6, 9);
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<double>(za, m, c->stream); }));
+    auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 6, 6, 9);
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = b;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf, Tf>(ia, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
   }
   return HOM_OK;
 }
 
-template <typename Tf>
 hom_status export_field(hom_ctx* c, int order, int load, int kind, double* d) {
   const OrderData& o = c->ord[order];
   const long long M = c->g.M;
+  const double* eps = reinterpret_cast<const double*>(o.eps) + (long long)load * 6 * M;
   if (kind == HOM_FIELD_STRAIN) {
-    CK(launch_kelvin_to_mandel<Tf>(reinterpret_cast<const Tf*>(o.eps) + (long long)load * 6 * M, d, M, 1,
-                                   c->stream));
+    CK(launch_kelvin_to_mandel<double>(eps, d, M, 1, c->stream));
   } else if (kind == HOM_FIELD_DISPLACEMENT) {
-    CK((launch_convert<Tf, double>(reinterpret_cast<const Tf*>(o.disp) + (long long)load * 3 * M, d, 3 * M,
-                                   c->stream)));
+    CK(cudaMemcpyAsync(d, reinterpret_cast<const double*>(o.disp) + (long long)load * 3 * M, sizeof(double) * 3 * M,
+                       cudaMemcpyDeviceToDevice, c->stream));
   } else {
     const double* ek = nullptr;
     if (order == 0) {
       CK(cudaMemcpyAsync(c->d_E, &o.loadsK[load * 6], sizeof(double) * 6, cudaMemcpyHostToDevice, c->stream));
       ek = c->d_E;
     }
-    CK(launch_stress_field<Tf>(reinterpret_cast<const Tf*>(o.eps) + (long long)load * 6 * M, ek,
-                               order > 0 ? reinterpret_cast<const Tf*>(o.pf) + (long long)load * 6 * M : nullptr,
-                               c->d_phase, c->d_mat64, M, d, c->stream));
+    CK(launch_stress_field<double>(eps, ek,
+                                   order > 0 ? reinterpret_cast<const double*>(o.pf) + (long long)load * 6 * M : nullptr,
+                                   c->d_phase, c->d_mat64, M, d, c->stream));
   }
   return HOM_OK;
 }
@@ -721,11 +727,10 @@ hom_status solve_order0(hom_ctx* c, int n, const double* loads, double tol, hom_
   }
   CKS(ensure_cap(c, n));
   CK(cudaMemcpyAsync(c->d_E, o.loadsK.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice, c->stream));
-  hom_status s = solve_system<Tf, Tf>(c, n, c->d_E, nullptr, reinterpret_cast<Tf*>(o.eps), tol, info);
+  hom_status s = solve_system<Tf>(c, n, c->d_E, nullptr, reinterpret_cast<double*>(o.eps), tol, info);
   if (s != HOM_OK && s != HOM_ERR_NOT_CONVERGED) return s;
-  CKS(mean_stress<Tf>(c, 0, o.eff));
-  hom_status sd = displacements<Tf>(c, 0);
-  if (sd != HOM_OK) return sd;
+  CKS(mean_stress(c, 0, o.eff));
+  CKS(displacements(c, 0));
   o.solved = (s == HOM_OK);
   return s;
 }
@@ -739,13 +744,13 @@ hom_status solve_higher(hom_ctx* c, int order, double tol, hom_solve_info* info)
   OrderData& o = c->ord[order];
   o.solved = false;
   void* vb;
-  CKS(work(c, 2, field_bytes(c, n, 6), &vb));
-  Tf* b = reinterpret_cast<Tf*>(vb);
-  CKS(build_rhs<Tf>(c, order, b, reinterpret_cast<Tf*>(o.pf)));
-  hom_status s = solve_system<Tf, Tf>(c, n, nullptr, b, reinterpret_cast<Tf*>(o.eps), tol, info);
+  CKS(work(c, 2, tbytes<double>(c, n, 6), &vb));
+  double* b = reinterpret_cast<double*>(vb);
+  CKS(build_rhs(c, order, b, reinterpret_cast<double*>(o.pf)));
+  hom_status s = solve_system<Tf>(c, n, nullptr, b, reinterpret_cast<double*>(o.eps), tol, info);
   if (s != HOM_OK && s != HOM_ERR_NOT_CONVERGED) return s;
-  CKS(mean_stress<Tf>(c, order, o.eff));
-  CKS(displacements<Tf>(c, order));
+  CKS(mean_stress(c, order, o.eff));
+  CKS(displacements(c, order));
   o.solved = (s == HOM_OK);
   return s;
 }
@@ -971,7 +976,8 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     const size_t b64 = (size_t)6 * n3 * (size_t)g.plane_c * sizeof(cx<double>);
     c->chunk64 = (int)std::max<size_t>(1, budget / b64);
     c->chunk64 = std::min(c->chunk64, 64);
-    if ((s = dalloc(c, (void**)&c->d_S64, b64 * c->chunk64)) != HOM_OK) return bail(s);
+    c->S64_comps = std::max(6 * c->chunk64, 9);
+    if ((s = dalloc(c, (void**)&c->d_S64, b64 / 6 * c->S64_comps)) != HOM_OK) return bail(s);
   }
   if ((s = ensure_cap(c, 6)) != HOM_OK) return bail(s);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
@@ -1035,7 +1041,7 @@ HOM_API hom_status hom_get_field(hom_t c, int32_t order, int32_t load, int32_t k
     CKS(work(c, 2, std::max(nbytes, c->work_bytes[2]), &tmp));
     d = reinterpret_cast<double*>(tmp);
   }
-  hom_status s = c->fp32 ? export_field<float>(c, order, load, kind, d) : export_field<double>(c, order, load, kind, d);
+  hom_status s = export_field(c, order, load, kind, d);
   if (s != HOM_OK) return s;
   if (!dst_on_device) CK(cudaMemcpyAsync(dst, d, nbytes, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -98,8 +98,7 @@ struct InvArgs {
   int rhs0;
   T c0h, c0d;            // C0 Kelvin eigenvalues: 3 lam0 + 2 mu0, 2 mu0
   Tf* out;               // INV_STORE
-  const Tf* b;           // INV_STORE: added field (nullable)
-  const Tf* sub;         // INV_STORE: subtracted field (nullable)
+  const double* b;       // INV_STORE: added right-hand-side field, FP64 (nullable)
   const Tf* prev;        // INV_STORE: previous iterate for the Cauchy difference (nullable)
   const Tf* p;           // INV_CG
   Tf* x;                 // INV_CG

@@ -201,6 +201,5 @@ cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
 
 template cudaError_t launch_plane_fwd<float, float>(const FwdArgs<float, float>&, int, cudaStream_t);
 template cudaError_t launch_plane_fwd<double, double>(const FwdArgs<double, double>&, int, cudaStream_t);
-template cudaError_t launch_plane_fwd<float, double>(const FwdArgs<float, double>&, int, cudaStream_t);
 
 }  // namespace hom

@@ -24,8 +24,10 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   const cx<T>* Sp = a.S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
   if (a.prof != nullptr && tid == 0) {
     const long long psz = (long long)n2 * n1;
-    long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.b != nullptr) + (a.sub != nullptr) + (a.fin == FIN_BASIC);
-    atomicAdd(a.prof, (unsigned long long)(fields * psz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>)));
+    long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
+    long long b = fields * psz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>);
+    if (a.b != nullptr) b += psz * (long long)sizeof(double);
+    atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)psz);
   }
   const long long nmain = (long long)n2 * h;
@@ -80,8 +82,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
         const long long o = foff + (long long)row * n1 + 2 * c2;
         const cx<T> e = pl[row * P + c2];
         T v0 = e.re, v1 = e.im;
-        if (a.b != nullptr) { Tf b0, b1; ld2<Tf>(a.b + o, b0, b1); v0 += (T)b0; v1 += (T)b1; }
-        if (a.sub != nullptr) { Tf s0, s1; ld2<Tf>(a.sub + o, s0, s1); v0 -= (T)s0; v1 -= (T)s1; }
+        if (a.b != nullptr) { double b0, b1; ld2<double>(a.b + o, b0, b1); v0 += (T)b0; v1 += (T)b1; }
         if (a.fin == FIN_BASIC) {
           Tf p0, p1;
           ld2<Tf>(a.prev + o, p0, p1);
