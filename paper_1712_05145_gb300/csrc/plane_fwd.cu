@@ -58,13 +58,14 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
     }
   } else if (a.mode == FWD_CG) {
     const RhsState& s = a.st[rhs];
-    const T beta = s.restart ? (T)0 : (T)s.beta;
+    const bool restart = (s.restart != 0);
+    const T beta = restart ? (T)0 : (T)s.beta;
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = (long long)row * n1 + 2 * c2;
-        Tf r0, r1, p0, p1;
+        Tf r0, r1, p0 = 0, p1 = 0;
         ld2<Tf>(a.r + foff + o, r0, r1);
-        ld2<Tf>(a.p + foff + o, p0, p1);
+        if (!restart) ld2<Tf>(a.p + foff + o, p0, p1);   // a restart never reads the old p
         const T q0 = (T)r0 + beta * (T)p0;
         const T q1 = (T)r1 + beta * (T)p1;
         st2<Tf>(a.p + foff + o, (Tf)q0, (Tf)q1);

@@ -33,7 +33,7 @@ def test_orders_0_1_2_match_oracle(oracle_asym, precision):
     from paper_1712_05145_gb300 import hom
     ms, oh = oracle_asym
     H = hom.Homogenization(ms, precision=precision)
-    tol = 1e-12 if precision == 0 else 1e-7
+    tol = 1e-12 if precision == 0 else 1e-9
     for order in (0, 1, 2):
         info = H.solve(order, tol)
         assert all(i["status"] == 0 for i in info), (order, info)
