@@ -48,6 +48,21 @@ __global__ void kelvin_to_mandel_kernel(const Tf* __restrict__ in, double* __res
   }
 }
 
+// Kelvin -> Mandel of FP64 fields in place: each thread reads a voxel's 6 components before
+// writing them back (no restrict: input and output alias)
+__global__ void kelvin_to_mandel_inplace_kernel(double* f, long long M, int nf) {
+  const long long total = (long long)nf * M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / M, v = i - q * M;
+    double* a = f + q * 6 * M + v;
+    const double k0 = a[0], k1 = a[M], k2 = a[2 * M];
+    a[0] = k0 * R3 + k1 * R2 + k2 * R6;
+    a[M] = k0 * R3 - k1 * R2 + k2 * R6;
+    a[2 * M] = k0 * R3 - 2.0 * k2 * R6;
+  }
+}
+
 template <typename Ti, typename To>
 __global__ void convert_kernel(const Ti* __restrict__ in, To* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -70,6 +85,10 @@ cudaError_t launch_mandel_to_kelvin(const double* in, Tf* out, long long M, int 
 template <typename Tf>
 cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int nf, cudaStream_t s) {
   kelvin_to_mandel_kernel<Tf><<<grid_for(M * nf, 256), 256, 0, s>>>(in, out, M, nf);
+  return cudaGetLastError();
+}
+cudaError_t launch_kelvin_to_mandel_inplace(double* f, long long M, int nf, cudaStream_t s) {
+  kelvin_to_mandel_inplace_kernel<<<grid_for(M * nf, 256), 256, 0, s>>>(f, M, nf);
   return cudaGetLastError();
 }
 template <typename Ti, typename To>

@@ -168,34 +168,50 @@ template <typename T, int R, int DIR> struct SmallDFT {
 };
 
 // ---- Stockham autosort stage over pencils in shared memory ------------------
-// Pencil p, element n lives at buf[addr(p, n)].  Ns = product of the radices of the
-// earlier stages.  tw[t] = exp(-2 pi i t / N) (host-computed), conjugated for DIR=+1.
-// Each thread runs up to MAXT radix-R tasks; all loads of the stage complete
-// (barrier) before any store, so the stage works in place.
+// Pencil p, element n lives at buf[addr(p, n)].  N (axis length) and NS (product of the
+// radices of the earlier stages) are compile-time constants.  tw[t] = exp(-2 pi i t / N)
+// (host-computed, usually staged in shared memory), conjugated for DIR = +1.  Each thread runs
+// up to MAXT radix-R tasks; task t covers pencil t mod npen and butterfly t div npen, so
+// consecutive threads touch consecutive pencils.  All loads of a stage complete (barrier)
+// before any store, so the stage works in place.
+
+// q = n / d for 0 <= n < 2^31 with a precomputed multiplier (Granlund-Montgomery round-up)
+struct FastDiv {
+  unsigned d, m, s;
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> s; }
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned s = 0;
+  while ((1u << s) < d) ++s;
+  const unsigned long long m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+  FastDiv f;
+  f.d = d;
+  f.m = (unsigned)m;
+  f.s = s;
+  return f;
+}
+
 struct RowAddr {   // pencils are rows: addr = p * pitch + n (odd pitch: conflict-free across rows)
   int pitch;
   __device__ __forceinline__ int operator()(int p, int n) const { return p * pitch + n; }
-  static constexpr bool pencil_fast = true;
 };
 struct ColAddr {   // pencils are columns: addr = p + n * pitch
   int pitch;
   __device__ __forceinline__ int operator()(int p, int n) const { return p + n * pitch; }
-  static constexpr bool pencil_fast = true;
 };
-struct ZAddr {     // pencil p = c * tc_n + tc (tc_n a power of two): addr = c*cstride + n*tcp + tc
+struct ZAddr {     // pencil p = c * 2^tc_log2 + tc: addr = c*cstride + n*tcp + tc
   int tc_log2, cstride, tcp;
   __device__ __forceinline__ int operator()(int p, int n) const {
     return (p >> tc_log2) * cstride + n * tcp + (p & ((1 << tc_log2) - 1));
   }
-  static constexpr bool pencil_fast = true;
 };
 
-template <typename T, int R, int DIR, int MAXT, typename Addr>
-__device__ __forceinline__ void stockham_stage(cx<T>* buf, const Addr& addr, int N, int Ns,
-                                               int npen, const cx<T>* __restrict__ tw) {
-  const int per = N / R;
+template <typename T, int N, int NS, int R, int DIR, int MAXT, typename Addr>
+__device__ __forceinline__ void stockham_stage(cx<T>* buf, const Addr& addr, int npen, const FastDiv& npd,
+                                               const cx<T>* tw) {
+  constexpr int per = N / R;
+  constexpr int tstep = N / (NS * R);
   const int ntask = npen * per;
-  const int tstep = N / (Ns * R);
   cx<T> v[MAXT][R];
   int pen[MAXT], base[MAXT];
 #pragma unroll
@@ -203,17 +219,16 @@ __device__ __forceinline__ void stockham_stage(cx<T>* buf, const Addr& addr, int
     const int t = threadIdx.x + i * blockDim.x;
     pen[i] = -1;
     if (t < ntask) {
-      int p, j;
-      if (Addr::pencil_fast) { p = t % npen; j = t / npen; }
-      else { p = t / per; j = t - p * per; }
+      const int j = (int)npd.div((unsigned)t);
+      const int p = t - j * npen;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[i][r] = buf[addr(p, j + r * per)];
-      const int k = j % Ns;
-      if (Ns > 1) {
+      const int k = j % NS;
+      if (NS > 1) {
         const int st = k * tstep;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          cx<T> w = ldg_cx(tw + st * r);
+          cx<T> w = tw[st * r];
           if (DIR > 0) w.im = -w.im;
           v[i][r] = cmul(v[i][r], w);
         }
@@ -228,29 +243,29 @@ __device__ __forceinline__ void stockham_stage(cx<T>* buf, const Addr& addr, int
   for (int i = 0; i < MAXT; ++i) {
     if (pen[i] >= 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[addr(pen[i], base[i] + r * Ns)] = v[i][r];
+      for (int r = 0; r < R; ++r) buf[addr(pen[i], base[i] + r * NS)] = v[i][r];
     }
   }
   __syncthreads();
 }
 
-// Fixed radix sequences, one per supported axis length.  Each length is a
-// straight-line run of stages (no runtime loop over stage kinds): register
-// allocation then takes the maximum over the stages rather than their union.
-template <typename T, int DIR, int EPT, int... Rs>
+// Fixed radix sequences, one per supported axis length.  Each length is a straight-line run
+// of stages (no runtime loop over stage kinds): register allocation then takes the maximum
+// over the stages rather than their union, and every stride is a compile-time constant.
+template <typename T, int DIR, int EPT, int N, int NS, int... Rs>
 struct StageSeq;
-template <typename T, int DIR, int EPT>
-struct StageSeq<T, DIR, EPT> {
+template <typename T, int DIR, int EPT, int N, int NS>
+struct StageSeq<T, DIR, EPT, N, NS> {
   template <typename Addr>
-  __device__ __forceinline__ static void run(cx<T>*, const Addr&, int, int, int, const cx<T>*) {}
+  __device__ __forceinline__ static void run(cx<T>*, const Addr&, int, const FastDiv&, const cx<T>*) {}
 };
-template <typename T, int DIR, int EPT, int R, int... Rs>
-struct StageSeq<T, DIR, EPT, R, Rs...> {
+template <typename T, int DIR, int EPT, int N, int NS, int R, int... Rs>
+struct StageSeq<T, DIR, EPT, N, NS, R, Rs...> {
   template <typename Addr>
-  __device__ __forceinline__ static void run(cx<T>* b, const Addr& a, int n, int ns, int npen,
+  __device__ __forceinline__ static void run(cx<T>* b, const Addr& a, int npen, const FastDiv& npd,
                                              const cx<T>* tw) {
-    stockham_stage<T, R, DIR, (EPT + R - 1) / R>(b, a, n, ns, npen, tw);
-    StageSeq<T, DIR, EPT, Rs...>::run(b, a, n, ns * R, npen, tw);
+    stockham_stage<T, N, NS, R, DIR, (EPT + R - 1) / R>(b, a, npen, npd, tw);
+    StageSeq<T, DIR, EPT, N, NS * R, Rs...>::run(b, a, npen, npd, tw);
   }
 };
 
@@ -261,31 +276,34 @@ __host__ __device__ constexpr bool fft_length_supported(int n) {
          n == 384 || n == 512;
 }
 
-// Runs the FFT of length n on `npen` pencils.  EPT bounds elements per thread:
-// the caller guarantees npen * n <= EPT * blockDim.x.
+// Runs the FFT of length n on `npen` pencils (npd divides by npen).  EPT bounds elements per
+// thread: the caller guarantees npen * n <= EPT * blockDim.x.
 template <typename T, int DIR, int EPT, typename Addr>
-__device__ __forceinline__ void fft_pencils(cx<T>* buf, const Addr& addr, int n, int npen,
-                                            const cx<T>* __restrict__ tw) {
+__device__ __forceinline__ void fft_pencils(cx<T>* buf, const Addr& addr, int n, int npen, const FastDiv& npd,
+                                            const cx<T>* tw) {
+#define HOM_SEQ(NN, ...) \
+  case NN: StageSeq<T, DIR, EPT, NN, 1, __VA_ARGS__>::run(buf, addr, npen, npd, tw); break;
   switch (n) {
-    case 2: StageSeq<T, DIR, EPT, 2>::run(buf, addr, n, 1, npen, tw); break;
-    case 3: StageSeq<T, DIR, EPT, 3>::run(buf, addr, n, 1, npen, tw); break;
-    case 4: StageSeq<T, DIR, EPT, 4>::run(buf, addr, n, 1, npen, tw); break;
-    case 6: StageSeq<T, DIR, EPT, 6>::run(buf, addr, n, 1, npen, tw); break;
-    case 8: StageSeq<T, DIR, EPT, 8>::run(buf, addr, n, 1, npen, tw); break;
-    case 12: StageSeq<T, DIR, EPT, 12>::run(buf, addr, n, 1, npen, tw); break;
-    case 16: StageSeq<T, DIR, EPT, 16>::run(buf, addr, n, 1, npen, tw); break;
-    case 24: StageSeq<T, DIR, EPT, 8, 3>::run(buf, addr, n, 1, npen, tw); break;
-    case 32: StageSeq<T, DIR, EPT, 8, 4>::run(buf, addr, n, 1, npen, tw); break;
-    case 48: StageSeq<T, DIR, EPT, 16, 3>::run(buf, addr, n, 1, npen, tw); break;
-    case 64: StageSeq<T, DIR, EPT, 16, 4>::run(buf, addr, n, 1, npen, tw); break;
-    case 96: StageSeq<T, DIR, EPT, 16, 6>::run(buf, addr, n, 1, npen, tw); break;
-    case 128: StageSeq<T, DIR, EPT, 16, 8>::run(buf, addr, n, 1, npen, tw); break;
-    case 192: StageSeq<T, DIR, EPT, 16, 12>::run(buf, addr, n, 1, npen, tw); break;
-    case 256: StageSeq<T, DIR, EPT, 16, 16>::run(buf, addr, n, 1, npen, tw); break;
-    case 384: StageSeq<T, DIR, EPT, 16, 8, 3>::run(buf, addr, n, 1, npen, tw); break;
-    case 512: StageSeq<T, DIR, EPT, 8, 8, 8>::run(buf, addr, n, 1, npen, tw); break;
+    HOM_SEQ(2, 2)
+    HOM_SEQ(3, 3)
+    HOM_SEQ(4, 4)
+    HOM_SEQ(6, 6)
+    HOM_SEQ(8, 8)
+    HOM_SEQ(12, 12)
+    HOM_SEQ(16, 16)
+    HOM_SEQ(24, 8, 3)
+    HOM_SEQ(32, 8, 4)
+    HOM_SEQ(48, 16, 3)
+    HOM_SEQ(64, 16, 4)
+    HOM_SEQ(96, 16, 6)
+    HOM_SEQ(128, 16, 8)
+    HOM_SEQ(192, 16, 12)
+    HOM_SEQ(256, 16, 16)
+    HOM_SEQ(384, 16, 8, 3)
+    HOM_SEQ(512, 8, 8, 8)
     default: break;
   }
+#undef HOM_SEQ
 }
 
 // ---- FP64 block reduction ---------------------------------------------------

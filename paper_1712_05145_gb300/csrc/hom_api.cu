@@ -212,6 +212,8 @@ FwdArgs<Tf, T> fwd_args(hom_ctx* c, int mode, int ncomp, int in_ncomp) {
   a.phase = c->d_phase;
   a.mat = mat_ptr<T>(c);
   a.n_phase = c->nphase;
+  a.c0h = (T)(3.0 * c->lam0 + 2.0 * c->mu0);
+  a.c0d = (T)(2.0 * c->mu0);
   a.part = part_fwd(c);
   a.cnt = cnt_fwd(c);
   a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_PLANE_FWD : nullptr;
@@ -246,6 +248,7 @@ InvArgs<Tf, T> inv_args(hom_ctx* c, int mode, int fin, int ncomp, int out_ncomp,
   a.s_ncomp = s_ncomp;
   a.c0h = (T)(3.0 * c->lam0 + 2.0 * c->mu0);
   a.c0d = (T)(2.0 * c->mu0);
+  a.out_scale = (T)1;
   a.part = part_inv(c);
   a.cnt = cnt_inv(c);
   a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_PLANE_INV : nullptr;
@@ -356,6 +359,23 @@ size_t tbytes(const hom_ctx* c, int nf, int ncomp) {
   return (size_t)nf * ncomp * (size_t)c->g.M * sizeof(Tf);
 }
 
+// x <- Gamma0 * (C0 : x), the C0-orthogonal projection onto compatible fields, in FP64.  The
+// FP32 corrections carry rounding noise that is not compatible; left in x, the compatible-
+// subspace residual below would turn it into a compatible error scaled by the stiffness
+// contrast.  Projected, x differs from the solution only by compatible errors the residual sees.
+hom_status project_compatible(hom_ctx* c, int n, double* x64, const std::vector<int>* act) {
+  auto fa = fwd_args<double, double>(c, FWD_C0, 6, 6);
+  fa.in = x64;
+  fa.st = c->d_st;
+  auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+  za.st = c->d_st;
+  auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 6, 6, 6);
+  ia.out = x64;
+  ia.out_scale = -1.0;
+  ia.st = c->d_st;
+  return ls_pass<double, double, double>(c, n, fa, za, ia, act);
+}
+
 // FP64 residual sweep r = b - A x, evaluated as b - Gamma0 * (C : (x + E)) (Eq. cg_form with
 // A = Gamma0 * C on compatible fields): equal to the literal residual on compatible x, and
 // itself exactly compatible, so CG restarts inside the subspace where A is self-adjoint in the
@@ -409,6 +429,8 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
     s.max_iter = c->opt.max_iter;
     s.active = 1;
     s.restart = 1;
+    s.best = 1e300;
+    s.best_iter = 0;
     st[i] = s;
   }
   CKS(write_states(c, st));
@@ -468,6 +490,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
     for (int i = 0; i < n; ++i) st[i].active = 1;
     CKS(write_states(c, st));
     std::vector<int> all(n, 1);
+    if (mixed) CKS(project_compatible(c, n, x64, &all));
     CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &all));
     CKS(read_states(c, n, st));
     for (int i = 0; i < n; ++i) {
@@ -541,6 +564,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
       }
       if (!need) break;
       CKS(write_states(c, st));
+      if (mixed) CKS(project_compatible(c, n, x64, &act));
       CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       CKS(read_states(c, n, st));
       bool again = false;
@@ -553,6 +577,8 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
           refine[i] += 1;
           st[i].active = 1;  // restart CG from the FP64 residual
           st[i].tol = mixed ? std::max(0.5 * tol, kSweepGain * st[i].res_true) : 0.5 * tol;
+          st[i].best = 1e300;
+          st[i].best_iter = st[i].iter;
           again = true;
         } else {
           st[i].active = 0;
@@ -909,12 +935,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   g.P = (g.h & 1) ? g.h : g.h + 1;
   g.M = (long long)n1 * n2 * n3;
   g.plane_c = (long long)n2 * (g.h + 1);
-  {
-    const long long e = (long long)n2 * g.h;
-    int thr = (int)((e + 15) / 16);
-    thr = ((thr + 31) / 32) * 32;
-    g.thr_plane = std::max(128, std::min(512, thr));
-  }
+  geo_finish(g);
   const int nmax = std::max(n1, std::max(n2, n3));
   g.xs1 = 2.0 * M_PI * nmax / n1;
   g.xs2 = 2.0 * M_PI * nmax / n2;

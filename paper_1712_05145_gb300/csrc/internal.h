@@ -18,6 +18,7 @@ struct Geo {
   long long M;           // voxels
   long long plane_c;     // n2 * (h + 1)
   int thr_plane;         // threads per CTA of the plane kernels
+  FastDiv fd_h, fd_n2;   // division by h and n2 (pencil counts of the column and row FFTs)
   double xs1, xs2, xs3;  // physical frequency per integer wave number: 2 pi Nmax / N_i
 };
 
@@ -30,19 +31,21 @@ struct RhsState {
   double res;        // latest relative residual (recursive / Cauchy)
   double res_true;   // FP64 residual ||b - A x|| / ||b||
   double tol;        // inner stopping tolerance
+  double best;       // smallest residual of the current sweep (stall detection)
   int iter;          // iterations done
   int max_iter;
   int active;        // 1 while the inner iteration runs
   int restart;       // 1: next CG step starts from p = r
   int status;        // 0 ok, 1 not converged, 2 numeric
-  int pad_;
+  int best_iter;     // iteration at which `best` was last halved
 };
 
 // FWD_TAU: tau = (C - C0) : (in + E)     (polarization, Eq. auxiliary_problem)
 // FWD_STRESS: tau = C : (in + E)         (stress; -Gamma0 * sigma is the equilibrium residual)
 // FWD_CG: p = r + beta p, tau = C : p    (CG direction; A p = Gamma0 * (C : p) on compatible p)
 // FWD_COPY: tau = in                     (plain transform)
-enum FwdMode { FWD_TAU = 0, FWD_CG = 1, FWD_COPY = 2, FWD_STRESS = 3 };
+// FWD_C0: tau = C0 : in                  (-Gamma0 * (C0 : in) is minus the compatible part of in)
+enum FwdMode { FWD_TAU = 0, FWD_CG = 1, FWD_COPY = 2, FWD_STRESS = 3, FWD_C0 = 4 };
 // Z_GAMMA: forward z FFT, -Gamma0_hat contraction, inverse z FFT (the LS step)
 // Z_FWD / Z_INV: forward / inverse z FFT only; Z_GREEN: contraction only (no FFT)
 // Z_DISP: forward z FFT of a strain, displacement u_hat (3 components), inverse z FFT
@@ -57,6 +60,7 @@ struct FwdArgs {
   int mode, ncomp, in_ncomp;   // components transformed; components per rhs of `in`
   const uint8_t* phase;
   const T* mat;                // [n_phase][4] Kelvin eigenvalues: C-C0 (h, dev), C (h, dev)
+  T c0h, c0d;                  // FWD_C0: C0 Kelvin eigenvalues 3 lam0 + 2 mu0, 2 mu0
   int n_phase;
   const Tf* in;                // FWD_TAU: strain (nullable); FWD_COPY: field
   const double* E;             // FWD_TAU: [rhs][6] Kelvin macroscopic strain (nullable)
@@ -80,6 +84,8 @@ struct ZArgs {
   int tc_log2;           // tile: 2^tc_log2 consecutive spectrum columns
   int ntiles;            // ceil(plane_c / 2^tc_log2)
   int nthr;              // threads per CTA
+  int cstride;           // shared-memory stride between components (padded against bank conflicts)
+  FastDiv fd_in, fd_out; // division by ncomp_in * 2^tc_log2 and ncomp_out * 2^tc_log2
   cx<T>* S;
   int rhs0;
   const RhsState* st;
@@ -97,6 +103,7 @@ struct InvArgs {
   const cx<T>* S;
   int rhs0;
   T c0h, c0d;            // C0 Kelvin eigenvalues: 3 lam0 + 2 mu0, 2 mu0
+  T out_scale;           // INV_STORE: out = out_scale * eta (+ b)
   Tf* out;               // INV_STORE
   const double* b;       // INV_STORE: added right-hand-side field, FP64 (nullable)
   const Tf* prev;        // INV_STORE: previous iterate for the Cauchy difference (nullable)
@@ -121,6 +128,8 @@ cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s);
 
 size_t plane_smem_bytes(const Geo& g, size_t elem);
 size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2);
+// fills fd_h, fd_n2 and thr_plane of a geometry whose n1, n2, n3 are set
+void geo_finish(Geo& g);
 // z-pass tiling for ncomp input components: fills tc_log2, ntiles, nthr
 template <typename T>
 void zpass_tiling(ZArgs<T>& a);

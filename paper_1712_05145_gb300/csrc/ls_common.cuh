@@ -19,6 +19,9 @@
 namespace hom {
 
 constexpr int kEPT = 16;
+// a CG sweep whose residual has not halved for this many iterations ends (the FP64
+// residual sweep then restarts it, or reports non-convergence)
+constexpr int kStallIters = 100;
 
 // ---------------------------------------------------------------------------------
 // small helpers
@@ -95,6 +98,8 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
       if (!isfinite(s.res) || !isfinite(s.beta)) { s.status = 2; s.active = 0; }
       else if (s.res < s.tol) s.active = 0;
       else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }
+      else if (s.res < 0.5 * s.best) { s.best = s.res; s.best_iter = s.iter; }
+      else if (s.iter - s.best_iter >= kStallIters) s.active = 0;  // sweep stalled: hand over to FP64
       break;
     }
     case FIN_BASIC: {
@@ -127,8 +132,13 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
   }
 }
 
+// Dynamic shared memory above 48 KB needs an opt-in; the carveout asks for the largest shared
+// memory partition so that the occupancy is not limited by a small default carveout.
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   if (bytes > 48 * 1024)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;

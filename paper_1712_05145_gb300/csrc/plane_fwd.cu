@@ -15,29 +15,35 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   const int n1 = g.n1, n2 = g.n2, h = g.h, P = g.P;
   cx<T>* pl = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* nyq = pl + n2 * P;
-  T* tab = reinterpret_cast<T*>(nyq + n2);
-  size_t off = align16((size_t)(n2 * P + n2) * sizeof(cx<T>) + 2 * a.n_phase * sizeof(T));
+  cx<T>* twh = nyq + n2;       // rows: exp(-2 pi i t / h)
+  cx<T>* twy = twh + h;        // columns: exp(-2 pi i t / n2)
+  cx<T>* tw1 = twy + n2;       // R2C split: exp(-2 pi i k / n1), k <= h
+  T* tab = reinterpret_cast<T*>(tw1 + h + 1);
+  size_t off = align16((size_t)(n2 * P + n2 + 2 * h + n2 + 1) * sizeof(cx<T>) + 2 * a.n_phase * sizeof(T));
   double* sh = reinterpret_cast<double*>(smem_raw + off);
   int* flag = reinterpret_cast<int*>(sh + 64);
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
 
-  if (a.mode != FWD_COPY) {
+  for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
+  for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
+  for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
+  if (a.mode != FWD_COPY && a.mode != FWD_C0) {
     for (int i = tid; i < a.n_phase; i += nthr) {
       tab[i] = a.mat[i * 4 + (c == 0 ? 0 : 1)];                 // C - C0 eigenvalue
       tab[a.n_phase + i] = a.mat[i * 4 + (c == 0 ? 2 : 3)];     // C eigenvalue
     }
-    __syncthreads();
   }
+  __syncthreads();
 
   const long long plane_sz = (long long)n2 * n1;
   const long long foff = ((long long)(rhs * a.in_ncomp + c) * g.n3 + z) * plane_sz;
   if (a.prof != nullptr && tid == 0) {
     // algorithmic bytes: field planes read/written once, phase bytes, spectrum plane written
-    long long fields = (a.mode == FWD_CG) ? 3 : ((a.mode == FWD_COPY || a.in != nullptr) ? 1 : 0);
+    long long fields = (a.mode == FWD_CG) ? 3 : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
     long long b = fields * plane_sz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>);
-    if (a.mode != FWD_COPY) b += plane_sz;
+    if (a.mode != FWD_COPY && a.mode != FWD_C0) b += plane_sz;
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)plane_sz);
   }
@@ -75,20 +81,21 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
         pl[row * P + c2] = mk<T>(c0 * q0, c1 * q1);
       }
     }
-  } else {  // FWD_COPY
+  } else {  // FWD_COPY, FWD_C0
+    const T w = (a.mode == FWD_C0) ? (c == 0 ? a.c0h : a.c0d) : (T)1;
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = (long long)row * n1 + 2 * c2;
         Tf v0, v1;
         ld2<Tf>(a.in + foff + o, v0, v1);
-        pl[row * P + c2] = mk<T>((T)v0, (T)v1);
+        pl[row * P + c2] = mk<T>(w * (T)v0, w * (T)v1);
       }
     }
   }
   __syncthreads();
 
   // x axis: length-h complex FFT of the packed rows z[n] = x[2n] + i x[2n+1]
-  fft_pencils<T, -1, EPT>(pl, RowAddr{P}, h, n2, a.tw_h);
+  fft_pencils<T, -1, EPT>(pl, RowAddr{P}, h, n2, g.fd_n2, twh);
 
   // R2C split: X[k] = (Z[k] + conj Z[h-k])/2 - i W^k (Z[k] - conj Z[h-k])/2, W = e^{-2 pi i/n1}.
   // X[0] and X[n1/2] are real and share slot 0 as X[0] + i X[n1/2].
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
         R[k] = conj(R[k]);
       } else {
         const cx<T> za = R[k], zb = R[h - k];
-        const cx<T> wa = ldg_cx(a.tw_n1 + k), wb = ldg_cx(a.tw_n1 + (h - k));
+        const cx<T> wa = tw1[k], wb = tw1[h - k];
         // X[k]
         cx<T> e = (za + conj(zb)) * (T)0.5;
         cx<T> o = mul_i<T, -1>(za - conj(zb)) * (T)0.5;
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   __syncthreads();
 
   // y axis: columns kx = 0..h-1 (column 0 carries X[0] + i X[n1/2])
-  fft_pencils<T, -1, EPT>(pl, ColAddr{P}, n2, h, a.tw_n2);
+  fft_pencils<T, -1, EPT>(pl, ColAddr{P}, n2, h, g.fd_h, twy);
 
   // separate column 0 into the kx = 0 column (A) and the Nyquist column kx = n1/2 (B):
   // A[k] = (P[k] + conj P[-k])/2,  B[k] = (P[k] - conj P[-k])/(2i)
@@ -157,13 +164,24 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   }
 }
 
+void geo_finish(Geo& g) {
+  const long long e = (long long)g.n2 * g.h;
+  int thr = (int)((e + kEPT - 1) / kEPT);
+  thr = ((thr + 31) / 32) * 32;
+  g.thr_plane = thr < 128 ? 128 : (thr > 512 ? 512 : thr);
+  g.fd_h = make_fastdiv((unsigned)g.h);
+  g.fd_n2 = make_fastdiv((unsigned)g.n2);
+}
+
 size_t plane_smem_bytes(const Geo& g, size_t elem) {
-  size_t b = (size_t)(g.n2 * g.P + g.n2) * elem + 2 * 256 * elem;
+  size_t b = (size_t)(g.n2 * g.P + g.n2 + 2 * g.h + g.n2 + 1) * elem + 2 * 256 * elem;
   b = (b + 15) & ~size_t(15);
   return b + 64 * sizeof(double) + 16;
 }
 size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2) {
-  return (size_t)ncomp * g.n3 * ((size_t)1 << tc_log2) * elem;
+  const size_t tc = (size_t)1 << tc_log2;
+  const size_t cstride = g.n3 * tc + ((g.n3 % 2 == 0) ? tc : 0);
+  return ((size_t)ncomp * cstride + g.n3) * elem;
 }
 
 // Widest power-of-two tile (<= 16 columns) whose pencils fit kEPT elements per thread
@@ -178,6 +196,11 @@ void zpass_tiling(ZArgs<T>& a) {
   a.tc_log2 = lg;
   const long long tc = 1LL << lg;
   a.ntiles = (int)((a.g.plane_c + tc - 1) / tc);
+  // component stride = n3 * tc, padded to an odd multiple of tc so that the 2 to 4 components
+  // a warp touches fall in different shared-memory banks
+  a.cstride = (int)(a.g.n3 * tc + ((a.g.n3 % 2 == 0) ? tc : 0));
+  a.fd_in = make_fastdiv((unsigned)(a.ncomp_in * tc));
+  a.fd_out = make_fastdiv((unsigned)(a.ncomp_out * tc));
   const long long e = (long long)a.ncomp_in * a.g.n3 * tc;
   int thr = (int)((e + kEPT - 1) / kEPT);
   thr = ((thr + 31) / 32) * 32;

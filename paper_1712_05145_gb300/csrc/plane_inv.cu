@@ -15,11 +15,17 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   if (a.st != nullptr && a.st[rhs].active == 0) return;
   const int n1 = g.n1, n2 = g.n2, h = g.h, P = g.P;
   cx<T>* pl = reinterpret_cast<cx<T>*>(smem_raw);
-  size_t off = align16((size_t)(n2 * P + n2) * sizeof(cx<T>));
+  cx<T>* twh = pl + n2 * P + n2;   // rows: exp(-2 pi i t / h)
+  cx<T>* twy = twh + h;            // columns: exp(-2 pi i t / n2)
+  cx<T>* tw1 = twy + n2;           // C2R merge: exp(-2 pi i k / n1), k <= h
+  size_t off = align16((size_t)(n2 * P + n2 + 2 * h + n2 + 1) * sizeof(cx<T>));
   double* sh = reinterpret_cast<double*>(smem_raw + off);
   int* flag = reinterpret_cast<int*>(sh + 64);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
+  for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
+  for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
 
   const cx<T>* Sp = a.S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
   if (a.prof != nullptr && tid == 0) {
@@ -43,7 +49,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   }
   __syncthreads();
 
-  fft_pencils<T, +1, EPT>(pl, ColAddr{P}, n2, h, a.tw_n2);
+  fft_pencils<T, +1, EPT>(pl, ColAddr{P}, n2, h, g.fd_h, twy);
 
   // C2R merge: Z[k] = X[k] + conj X[h-k] + i W^{-k} (X[k] - conj X[h-k]),  W = e^{-2 pi i/n1};
   // slot 0 holds X[0] + i X[n1/2]
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
         R[k] = conj(R[k]) * (T)2;
       } else {
         const cx<T> xa = R[k], xb = R[h - k];
-        const cx<T> wa = conj(ldg_cx(a.tw_n1 + k)), wb = conj(ldg_cx(a.tw_n1 + (h - k)));
+        const cx<T> wa = conj(tw1[k]), wb = conj(tw1[h - k]);
         const cx<T> za = (xa + conj(xb)) + mul_i<T, 1>(cmul(wa, xa - conj(xb)));
         const cx<T> zb = (xb + conj(xa)) + mul_i<T, 1>(cmul(wb, xb - conj(xa)));
         R[k] = za;
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   }
   __syncthreads();
 
-  fft_pencils<T, +1, EPT>(pl, RowAddr{P}, h, n2, a.tw_h);
+  fft_pencils<T, +1, EPT>(pl, RowAddr{P}, h, n2, g.fd_n2, twh);
 
   // epilogue on the real plane: x[2n] = Re z[n], x[2n+1] = Im z[n]
   const long long plane_sz = (long long)n2 * n1;
@@ -81,7 +87,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = foff + (long long)row * n1 + 2 * c2;
         const cx<T> e = pl[row * P + c2];
-        T v0 = e.re, v1 = e.im;
+        T v0 = a.out_scale * e.re, v1 = a.out_scale * e.im;
         if (a.b != nullptr) { double b0, b1; ld2<double>(a.b + o, b0, b1); v0 += (T)b0; v1 += (T)b1; }
         if (a.fin == FIN_BASIC) {
           Tf p0, p1;

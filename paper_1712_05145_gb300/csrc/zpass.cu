@@ -73,8 +73,10 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
   const int TC = 1 << tc_log2, n3 = g.n3;
   const long long f0 = (long long)tile * TC;
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
-  const int cstride = n3 * TC;
+  const int cstride = a.cstride;
+  cx<T>* twz = buf + a.ncomp_in * cstride;   // exp(-2 pi i t / n3)
   const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < n3; i += nthr) twz[i] = ldg_cx(a.tw_n3 + i);
   cx<T>* Sr = a.S + (long long)lrhs * a.ncomp_in * n3 * g.plane_c;
   if (a.prof != nullptr && tid == 0) {
     const long long cols = (g.plane_c - f0 < TC) ? g.plane_c - f0 : TC;
@@ -82,14 +84,16 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
     atomicAdd(a.prof + 1, (unsigned long long)(n3 * cols));
   }
 
-  for (int e = tid; e < a.ncomp_in * n3 * TC; e += nthr) {
-    const int tc = e & (TC - 1), row = e >> tc_log2;
-    const long long f = f0 + tc;
-    buf[e] = (f < g.plane_c) ? Sr[(long long)row * g.plane_c + f] : mk<T>(0, 0);
+  for (int c = 0; c < a.ncomp_in; ++c) {
+    for (int e = tid; e < n3 * TC; e += nthr) {
+      const int tc = e & (TC - 1), n = e >> tc_log2;
+      const long long f = f0 + tc;
+      buf[c * cstride + e] = (f < g.plane_c) ? Sr[(long long)(c * n3 + n) * g.plane_c + f] : mk<T>(0, 0);
+    }
   }
   __syncthreads();
   const ZAddr za{tc_log2, cstride, TC};
-  if (a.mode != Z_INV && a.mode != Z_GREEN) fft_pencils<T, -1, EPT>(buf, za, n3, a.ncomp_in * TC, a.tw_n3);
+  if (a.mode != Z_INV && a.mode != Z_GREEN) fft_pencils<T, -1, EPT>(buf, za, n3, a.ncomp_in * TC, a.fd_in, twz);
 
   if (a.mode == Z_GAMMA || a.mode == Z_GREEN || a.mode == Z_DISP || a.mode == Z_RHS) {
     const T c1 = (T)(1.0 / (2.0 * a.mu0));
@@ -142,12 +146,14 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
     __syncthreads();
   }
 
-  if (a.mode != Z_FWD && a.mode != Z_GREEN) fft_pencils<T, +1, EPT>(buf, za, n3, a.ncomp_out * TC, a.tw_n3);
+  if (a.mode != Z_FWD && a.mode != Z_GREEN) fft_pencils<T, +1, EPT>(buf, za, n3, a.ncomp_out * TC, a.fd_out, twz);
 
-  for (int e = tid; e < a.ncomp_out * n3 * TC; e += nthr) {
-    const int tc = e & (TC - 1), row = e >> tc_log2;
-    const long long f = f0 + tc;
-    if (f < g.plane_c) Sr[(long long)row * g.plane_c + f] = buf[e];
+  for (int c = 0; c < a.ncomp_out; ++c) {
+    for (int e = tid; e < n3 * TC; e += nthr) {
+      const int tc = e & (TC - 1), n = e >> tc_log2;
+      const long long f = f0 + tc;
+      if (f < g.plane_c) Sr[(long long)(c * n3 + n) * g.plane_c + f] = buf[c * cstride + e];
+    }
   }
 }
 
