@@ -98,8 +98,8 @@ struct hom_ctx {
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
-  double prof_ms[HOM_KERNEL_COUNT] = {0, 0, 0};
-  long long prof_launches[HOM_KERNEL_COUNT] = {0, 0, 0};
+  double prof_ms[HOM_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  long long prof_launches[HOM_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -216,7 +216,7 @@ FwdArgs<Tf, T> fwd_args(hom_ctx* c, int mode, int ncomp, int in_ncomp) {
   a.c0d = (T)(2.0 * c->mu0);
   a.part = part_fwd(c);
   a.cnt = cnt_fwd(c);
-  a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_PLANE_FWD : nullptr;
+  a.prof = c->prof_on ? c->d_prof + 2 * (HOM_KERNEL_PLANE_FWD + (sizeof(T) == 8 ? 3 : 0)) : nullptr;
   a.tw_h = tw<T>(c, 0);
   a.tw_n1 = tw<T>(c, 1);
   a.tw_n2 = tw<T>(c, 2);
@@ -232,7 +232,7 @@ ZArgs<T> z_args(hom_ctx* c, int mode, int nin, int nout) {
   a.lam0 = c->lam0;
   a.mu0 = c->mu0;
   a.scale = 1.0 / (double)c->g.M;
-  a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_ZPASS : nullptr;
+  a.prof = c->prof_on ? c->d_prof + 2 * (HOM_KERNEL_ZPASS + (sizeof(T) == 8 ? 3 : 0)) : nullptr;
   a.tw_n3 = tw<T>(c, 3);
   zpass_tiling<T>(a);
   return a;
@@ -251,7 +251,7 @@ InvArgs<Tf, T> inv_args(hom_ctx* c, int mode, int fin, int ncomp, int out_ncomp,
   a.out_scale = (T)1;
   a.part = part_inv(c);
   a.cnt = cnt_inv(c);
-  a.prof = c->prof_on ? c->d_prof + 2 * HOM_KERNEL_PLANE_INV : nullptr;
+  a.prof = c->prof_on ? c->d_prof + 2 * (HOM_KERNEL_PLANE_INV + (sizeof(T) == 8 ? 3 : 0)) : nullptr;
   a.tw_h = tw<T>(c, 0);
   a.tw_n1 = tw<T>(c, 1);
   a.tw_n2 = tw<T>(c, 2);
@@ -298,6 +298,10 @@ hom_status prof_drain(hom_ctx* c) {
   return HOM_OK;
 }
 
+// profile kind of an LS-step kernel transforming in precision T
+template <typename T>
+int kind_of(int k) { return k + (sizeof(T) == 8 ? 3 : 0); }
+
 // Launches one LS-step kernel; while accounting is on, brackets it with CUDA events.
 template <typename F>
 hom_status timed_launch(hom_ctx* c, int kind, F&& launch) {
@@ -336,9 +340,9 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArg
     fa.S = S;
     za.S = S;
     ia.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<Tf1, T>(fa, n, c->stream); }));
-    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<T>(za, n, c->stream); }));
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<Tf3, T>(ia, n, c->stream); }));
+    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_plane_fwd<Tf1, T>(fa, n, c->stream); }));
+    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(za, n, c->stream); }));
+    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_plane_inv<Tf3, T>(ia, n, c->stream); }));
   }
   return HOM_OK;
 }
@@ -670,16 +674,16 @@ hom_status displacements(hom_ctx* c, int order) {
     fa.in = reinterpret_cast<const double*>(o.eps);
     fa.rhs0 = r0;
     fa.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD_F64, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
     auto za = z_args<double>(c, Z_DISP, 6, 3);
     za.S = S;
     za.rhs0 = r0;
-    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<double>(za, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS_F64, [&] { return launch_zpass<double>(za, m, c->stream); }));
     auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 3, 3, 6);
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = reinterpret_cast<double*>(o.disp);
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV_F64, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
   }
   o.disp_ok = true;
   return HOM_OK;
@@ -710,16 +714,16 @@ hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf) {
     fa.in = f9;
     fa.rhs0 = r0;
     fa.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD_F64, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
     auto za = z_args<double>(c, Z_RHS, 9, 6);
     za.S = S;
     za.rhs0 = r0;
-    CKS(timed_launch(c, HOM_KERNEL_ZPASS, [&] { return launch_zpass<double>(za, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_ZPASS_F64, [&] { return launch_zpass<double>(za, m, c->stream); }));
     auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 6, 6, 9);
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = b;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
+    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV_F64, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
   }
   return HOM_OK;
 }
@@ -862,7 +866,7 @@ HOM_API hom_status hom_profile(hom_t c, int32_t enable) {
 HOM_API hom_status hom_profile_read(hom_t c, hom_kernel_stat* out) {
   if (!c || !out) return HOM_ERR_ARG;
   CKS(prof_drain(c));
-  unsigned long long hp[2 * HOM_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  unsigned long long hp[2 * HOM_KERNEL_COUNT] = {};
   if (c->d_prof) {
     CK(cudaMemcpyAsync(hp, c->d_prof, sizeof(hp), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));

@@ -86,6 +86,7 @@ struct ZArgs {
   int nthr;              // threads per CTA
   int cstride;           // shared-memory stride between components (padded against bank conflicts)
   FastDiv fd_in, fd_out; // division by ncomp_in * 2^tc_log2 and ncomp_out * 2^tc_log2
+  FastDiv fd_comp;       // division by n3 * 2^tc_log2 (elements of one component in a tile)
   cx<T>* S;
   int rhs0;
   const RhsState* st;

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   if (a.mode == FWD_TAU || a.mode == FWD_STRESS) {
     const T ec = (a.E != nullptr) ? (T)a.E[rhs * 6 + c] : (T)0;
     const T* w = (a.mode == FWD_TAU) ? tab : tab + a.n_phase;
+    #pragma unroll 4
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = (long long)row * n1 + 2 * c2;
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
     const RhsState& s = a.st[rhs];
     const bool restart = (s.restart != 0);
     const T beta = restart ? (T)0 : (T)s.beta;
+    #pragma unroll 4
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = (long long)row * n1 + 2 * c2;
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
     }
   } else {  // FWD_COPY, FWD_C0
     const T w = (a.mode == FWD_C0) ? (c == 0 ? a.c0h : a.c0d) : (T)1;
+    #pragma unroll 4
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = (long long)row * n1 + 2 * c2;
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   __syncthreads();
 
   cx<T>* Sp = a.S + ((long long)(lrhs * a.ncomp + c) * g.n3 + z) * g.plane_c;
+  #pragma unroll 4
   for (int row = warp; row < n2; row += nwarp)
     for (int col = lane; col < h; col += 32) Sp[(long long)row * h + col] = pl[row * P + col];
   for (int ky = tid; ky < n2; ky += nthr) Sp[(long long)n2 * h + ky] = nyq[ky];
@@ -201,6 +205,7 @@ void zpass_tiling(ZArgs<T>& a) {
   a.cstride = (int)(a.g.n3 * tc + ((a.g.n3 % 2 == 0) ? tc : 0));
   a.fd_in = make_fastdiv((unsigned)(a.ncomp_in * tc));
   a.fd_out = make_fastdiv((unsigned)(a.ncomp_out * tc));
+  a.fd_comp = make_fastdiv((unsigned)(a.g.n3 * tc));
   const long long e = (long long)a.ncomp_in * a.g.n3 * tc;
   int thr = (int)((e + kEPT - 1) / kEPT);
   thr = ((thr + 31) / 32) * 32;

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
     atomicAdd(a.prof + 1, (unsigned long long)psz);
   }
   const long long nmain = (long long)n2 * h;
+  #pragma unroll 4
   for (int row = warp; row < n2; row += nwarp) {
     for (int col = lane; col < h; col += 32) {
       cx<T> v = Sp[(long long)row * h + col];
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   if (a.mode == INV_STORE) {
     const long long foff = ((long long)(rhs * a.out_ncomp + c) * g.n3 + z) * plane_sz;
     const T cw = (c == 0) ? c0h : c0d;
+    #pragma unroll 4
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = foff + (long long)row * n1 + 2 * c2;
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
     const long long foff = ((long long)(rhs * 6 + c) * g.n3 + z) * plane_sz;
     const T alpha = (T)a.st[rhs].alpha;
     const T cw = (c == 0) ? c0h : c0d;
+    #pragma unroll 4
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {
         const long long o = foff + (long long)row * n1 + 2 * c2;

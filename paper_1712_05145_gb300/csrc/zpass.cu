@@ -84,12 +84,12 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
     atomicAdd(a.prof + 1, (unsigned long long)(n3 * cols));
   }
 
-  for (int c = 0; c < a.ncomp_in; ++c) {
-    for (int e = tid; e < n3 * TC; e += nthr) {
-      const int tc = e & (TC - 1), n = e >> tc_log2;
-      const long long f = f0 + tc;
-      buf[c * cstride + e] = (f < g.plane_c) ? Sr[(long long)(c * n3 + n) * g.plane_c + f] : mk<T>(0, 0);
-    }
+  const int per_c = n3 * TC;
+  for (int e = tid; e < a.ncomp_in * per_c; e += nthr) {
+    const int c = (int)a.fd_comp.div((unsigned)e), ec = e - c * per_c;
+    const int tc = ec & (TC - 1), n = ec >> tc_log2;
+    const long long f = f0 + tc;
+    buf[c * cstride + ec] = (f < g.plane_c) ? Sr[(long long)(c * n3 + n) * g.plane_c + f] : mk<T>(0, 0);
   }
   __syncthreads();
   const ZAddr za{tc_log2, cstride, TC};
@@ -148,12 +148,11 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
 
   if (a.mode != Z_FWD && a.mode != Z_GREEN) fft_pencils<T, +1, EPT>(buf, za, n3, a.ncomp_out * TC, a.fd_out, twz);
 
-  for (int c = 0; c < a.ncomp_out; ++c) {
-    for (int e = tid; e < n3 * TC; e += nthr) {
-      const int tc = e & (TC - 1), n = e >> tc_log2;
-      const long long f = f0 + tc;
-      if (f < g.plane_c) Sr[(long long)(c * n3 + n) * g.plane_c + f] = buf[c * cstride + e];
-    }
+  for (int e = tid; e < a.ncomp_out * per_c; e += nthr) {
+    const int c = (int)a.fd_comp.div((unsigned)e), ec = e - c * per_c;
+    const int tc = ec & (TC - 1), n = ec >> tc_log2;
+    const long long f = f0 + tc;
+    if (f < g.plane_c) Sr[(long long)(c * n3 + n) * g.plane_c + f] = buf[c * cstride + ec];
   }
 }
 

@@ -36,8 +36,8 @@ HOM_FIELD_STRESS = 2
 HOM_KERNEL_PLANE_FWD = 0
 HOM_KERNEL_ZPASS = 1
 HOM_KERNEL_PLANE_INV = 2
-HOM_KERNEL_COUNT = 3
-KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv"]
+HOM_KERNEL_COUNT = 6
+KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64", "plane_inv_f64"]
 
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
             "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
