@@ -71,7 +71,10 @@ typedef struct {
                               that the spectrum scratch fits l2_budget_bytes */
   int64_t l2_budget_bytes; /* target size of the spectrum scratch (0 = 64 MiB) */
   void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
-  int32_t reserved[8];
+  int32_t pass_mode;       /* x-y transforms: 0 = fused plane kernels when a plane fits one CTA,
+                              else split x and y passes; 1 = always fused (fails if a plane does
+                              not fit); 2 = always split */
+  int32_t reserved[7];
 } hom_options;
 
 typedef struct {
@@ -89,7 +92,8 @@ HOM_API void hom_default_options(hom_options* opt);
 
 /* Creates a handle for one voxel RVE (Sec. 2: C(x) piecewise isotropic, reference C0).
  *  grid[3]     N1, N2, N3.  N1 even with N1/2, N2 and N3 in {2,3,4,6,8,12,16,24,32,48,64,96,
- *              128,192,256,384,512}, and (N1/2) * N2 <= 8192 (one x-y plane per CTA).
+ *              128,192,256,384,512}.  Planes with (N1/2) * N2 <= 8192 can use the fused plane
+ *              kernels; larger ones use split x and y passes (hom_options.pass_mode).
  *  phase       uint8 [N3][N2][N1], host or device pointer (auto-detected); copied.
  *  n_phase     1..256; every phase index must be < n_phase.
  *  lame        double [n_phase][2] host array of (lambda, mu) per phase; copied.
@@ -155,7 +159,8 @@ HOM_API hom_status hom_green_apply(hom_t h, int32_t nrhs, const double* tau_hat,
 enum {
   HOM_KERNEL_PLANE_FWD = 0, HOM_KERNEL_ZPASS = 1, HOM_KERNEL_PLANE_INV = 2,
   HOM_KERNEL_PLANE_FWD_F64 = 3, HOM_KERNEL_ZPASS_F64 = 4, HOM_KERNEL_PLANE_INV_F64 = 5,
-  HOM_KERNEL_COUNT = 6
+  HOM_KERNEL_YPASS = 6, HOM_KERNEL_YPASS_F64 = 7,  /* split y pass (x passes count as plane kinds) */
+  HOM_KERNEL_COUNT = 8
 };
 
 typedef struct {

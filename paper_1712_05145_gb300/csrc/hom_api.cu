@@ -98,8 +98,8 @@ struct hom_ctx {
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
-  double prof_ms[HOM_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
-  long long prof_launches[HOM_KERNEL_COUNT] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[HOM_KERNEL_COUNT] = {};
+  long long prof_launches[HOM_KERNEL_COUNT] = {};
 };
 
 namespace {
@@ -166,10 +166,15 @@ hom_status work(hom_ctx* c, int i, size_t bytes, void** out) {
   return HOM_OK;
 }
 
+// partial sums one load's reducing kernel publishes at most (one per CTA)
+size_t ncta_max(const hom_ctx* c) {
+  return 6 * (size_t)std::max(c->g.n3, c->g.split ? c->g.nrb : 0) + 64;
+}
+
 // grows the per-load state, partial and load arrays to `n` loads
 hom_status ensure_cap(hom_ctx* c, int n) {
   if (n <= c->cap) return HOM_OK;
-  const size_t ncta = 6 * (size_t)c->g.n3 + 64;
+  const size_t ncta = ncta_max(c);
   if (c->d_st) {
     dfree(c, c->d_st, sizeof(RhsState) * c->cap);
     dfree(c, c->d_part, sizeof(double) * 2 * c->cap * 2 * ncta);
@@ -191,7 +196,7 @@ hom_status ensure_cap(hom_ctx* c, int n) {
 }
 
 double* part_fwd(hom_ctx* c) { return c->d_part; }
-double* part_inv(hom_ctx* c) { return c->d_part + (size_t)c->cap * 2 * (6 * (size_t)c->g.n3 + 64); }
+double* part_inv(hom_ctx* c) { return c->d_part + (size_t)c->cap * 2 * ncta_max(c); }
 unsigned* cnt_fwd(hom_ctx* c) { return c->d_cnt; }
 unsigned* cnt_inv(hom_ctx* c) { return c->d_cnt + c->cap; }
 
@@ -321,6 +326,33 @@ hom_status timed_launch(hom_ctx* c, int kind, F&& launch) {
   return HOM_OK;
 }
 
+// Forward x-y transform of one chunk: the fused plane kernel, or the split x and y passes.
+template <typename Tf, typename T>
+hom_status fwd_xy(hom_ctx* c, const FwdArgs<Tf, T>& fa, int n) {
+  if (!c->g.split)
+    return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_plane_fwd<Tf, T>(fa, n, c->stream); });
+  CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_xpass_fwd<Tf, T>(fa, n, c->stream); }));
+  const int yk = sizeof(T) == 8 ? HOM_KERNEL_YPASS_F64 : HOM_KERNEL_YPASS;
+  unsigned long long* yp = c->prof_on ? c->d_prof + 2 * yk : nullptr;
+  return timed_launch(c, yk, [&] {
+    return launch_ypass<T>(fa.tw_n2, fa.S, c->g, fa.ncomp, fa.ncomp, n, -1, yp, fa.st, fa.rhs0, c->stream);
+  });
+}
+
+// Inverse x-y transform of one chunk with the epilogue of `ia`.
+template <typename Tf, typename T>
+hom_status inv_xy(hom_ctx* c, const InvArgs<Tf, T>& ia, int n) {
+  if (!c->g.split)
+    return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_plane_inv<Tf, T>(ia, n, c->stream); });
+  const int yk = sizeof(T) == 8 ? HOM_KERNEL_YPASS_F64 : HOM_KERNEL_YPASS;
+  unsigned long long* yp = c->prof_on ? c->d_prof + 2 * yk : nullptr;
+  CKS(timed_launch(c, yk, [&] {
+    return launch_ypass<T>(ia.tw_n2, const_cast<cx<T>*>(ia.S), c->g, ia.ncomp, ia.s_ncomp, n, +1, yp, ia.st, ia.rhs0,
+                           c->stream);
+  }));
+  return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_xpass_inv<Tf, T>(ia, n, c->stream); });
+}
+
 // One full LS pass (plane_fwd, zpass, plane_inv) over loads [0, nrhs), chunk by chunk.  The
 // forward kernel reads fields of type Tf1, the inverse kernel writes fields of type Tf3, and the
 // transforms run in T.
@@ -340,9 +372,9 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArg
     fa.S = S;
     za.S = S;
     ia.S = S;
-    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_plane_fwd<Tf1, T>(fa, n, c->stream); }));
+    CKS(fwd_xy<Tf1, T>(c, fa, n));
     CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(za, n, c->stream); }));
-    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_plane_inv<Tf3, T>(ia, n, c->stream); }));
+    CKS(inv_xy<Tf3, T>(c, ia, n));
   }
   return HOM_OK;
 }
@@ -674,7 +706,7 @@ hom_status displacements(hom_ctx* c, int order) {
     fa.in = reinterpret_cast<const double*>(o.eps);
     fa.rhs0 = r0;
     fa.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD_F64, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
+    CKS((fwd_xy<double, double>(c, fa, m)));
     auto za = z_args<double>(c, Z_DISP, 6, 3);
     za.S = S;
     za.rhs0 = r0;
@@ -683,7 +715,7 @@ hom_status displacements(hom_ctx* c, int order) {
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = reinterpret_cast<double*>(o.disp);
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV_F64, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
+    CKS((inv_xy<double, double>(c, ia, m)));
   }
   o.disp_ok = true;
   return HOM_OK;
@@ -714,7 +746,7 @@ hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf) {
     fa.in = f9;
     fa.rhs0 = r0;
     fa.S = S;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_FWD_F64, [&] { return launch_plane_fwd<double, double>(fa, m, c->stream); }));
+    CKS((fwd_xy<double, double>(c, fa, m)));
     auto za = z_args<double>(c, Z_RHS, 9, 6);
     za.S = S;
     za.rhs0 = r0;
@@ -723,7 +755,7 @@ hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf) {
     ia.S = S;
     ia.rhs0 = r0;
     ia.out = b;
-    CKS(timed_launch(c, HOM_KERNEL_PLANE_INV_F64, [&] { return launch_plane_inv<double, double>(ia, m, c->stream); }));
+    CKS((inv_xy<double, double>(c, ia, m)));
   }
   return HOM_OK;
 }
@@ -904,7 +936,9 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if (n1 < 4 || (n1 & 1) || !fft_length_supported(n1 / 2) || !fft_length_supported(n2) ||
       !fft_length_supported(n3))
     return HOM_ERR_SIZE;
-  if ((long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
+  const int pass_mode = opt ? opt->pass_mode : 0;
+  if (pass_mode < 0 || pass_mode > 2) return HOM_ERR_ARG;
+  if (pass_mode == 1 && (long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
 
   c = new hom_ctx();
   hom_default_options(&c->opt);
@@ -940,6 +974,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   g.M = (long long)n1 * n2 * n3;
   g.plane_c = (long long)n2 * (g.h + 1);
   geo_finish(g);
+  g.split = (pass_mode == 2 || (pass_mode == 0 && (long long)g.n2 * g.h > 8192)) ? 1 : 0;
   const int nmax = std::max(n1, std::max(n2, n3));
   g.xs1 = 2.0 * M_PI * nmax / n1;
   g.xs2 = 2.0 * M_PI * nmax / n2;

@@ -19,6 +19,12 @@ struct Geo {
   long long plane_c;     // n2 * (h + 1)
   int thr_plane;         // threads per CTA of the plane kernels
   FastDiv fd_h, fd_n2;   // division by h and n2 (pencil counts of the column and row FFTs)
+  // split passes (grids whose x-y plane does not fit one CTA, or by choice):
+  int split;             // 1: x pass + y pass kernels instead of the fused plane kernels
+  int rb, nrb, thr_x;    // x pass: rows per CTA, row blocks per component, threads
+  FastDiv fd_rb;         // division by rb
+  int ty_log2, thr_y;    // y pass: 2^ty_log2 consecutive columns per CTA, threads
+  FastDiv fd_ty;         // division by 2^ty_log2
   double xs1, xs2, xs3;  // physical frequency per integer wave number: 2 pi Nmax / N_i
 };
 
@@ -122,6 +128,14 @@ struct InvArgs {
 
 template <typename Tf, typename T>
 cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s);
+// split passes: x pass (prologue + row R2C), y pass over column tiles, x inverse pass
+template <typename Tf, typename T>
+cudaError_t launch_xpass_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ypass(const cx<T>* tw_n2, cx<T>* S, const Geo& g, int ncomp, int s_ncomp, int nrhs, int dir,
+                         unsigned long long* prof, const RhsState* st, int rhs0, cudaStream_t s);
+template <typename Tf, typename T>
+cudaError_t launch_xpass_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zpass(const ZArgs<T>& a, int nrhs, cudaStream_t s);
 template <typename Tf, typename T>

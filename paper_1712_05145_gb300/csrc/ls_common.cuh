@@ -19,9 +19,12 @@
 namespace hom {
 
 constexpr int kEPT = 16;
-// a CG sweep whose residual has not halved for this many iterations ends (the FP64
-// residual sweep then restarts it, or reports non-convergence)
+// A CG sweep whose residual has not halved for kStallIters iterations ends (the FP64
+// residual sweep then restarts it, or reports non-convergence).  Below kNearFloor (relative
+// residual) an FP32 sweep is close to its rounding floor and a shorter window applies.
 constexpr int kStallIters = 100;
+constexpr int kStallItersNearFloor = 25;
+constexpr double kNearFloor = 1e-5;
 
 // ---------------------------------------------------------------------------------
 // small helpers
@@ -99,7 +102,8 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
       else if (s.res < s.tol) s.active = 0;
       else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }
       else if (s.res < 0.5 * s.best) { s.best = s.res; s.best_iter = s.iter; }
-      else if (s.iter - s.best_iter >= kStallIters) s.active = 0;  // sweep stalled: hand over to FP64
+      else if (s.iter - s.best_iter >= (s.res < kNearFloor ? kStallItersNearFloor : kStallIters))
+        s.active = 0;  // sweep stalled: hand over to the FP64 residual sweep
       break;
     }
     case FIN_BASIC: {

@@ -175,6 +175,25 @@ void geo_finish(Geo& g) {
   g.thr_plane = thr < 128 ? 128 : (thr > 512 ? 512 : thr);
   g.fd_h = make_fastdiv((unsigned)g.h);
   g.fd_n2 = make_fastdiv((unsigned)g.n2);
+  // split passes: x pass with rb rows of h values per CTA (<= kEPT * 256 elements),
+  // y pass with 2^ty_log2 columns (a power of two dividing h, <= 16) of n2 values per CTA
+  const long long nrows = (long long)g.n2 * g.n3;
+  long long rb = (kEPT * 256) / g.h;
+  if (rb < 1) rb = 1;
+  if (rb > nrows) rb = nrows;
+  g.rb = (int)rb;
+  g.nrb = (int)((nrows + rb - 1) / rb);
+  int tx = (int)((rb * g.h + kEPT - 1) / kEPT);
+  tx = ((tx + 31) / 32) * 32;
+  g.thr_x = tx < 64 ? 64 : tx;
+  g.fd_rb = make_fastdiv((unsigned)g.rb);
+  int lg = 0;
+  while (lg < 4 && (g.h % (2 << lg)) == 0 && (long long)g.n2 * (2 << lg) <= (long long)kEPT * 512) ++lg;
+  g.ty_log2 = lg;
+  int ty = (int)(((long long)g.n2 * (1 << lg) + kEPT - 1) / kEPT);
+  ty = ((ty + 31) / 32) * 32;
+  g.thr_y = ty < 64 ? 64 : ty;
+  g.fd_ty = make_fastdiv((unsigned)(1 << lg));
 }
 
 size_t plane_smem_bytes(const Geo& g, size_t elem) {

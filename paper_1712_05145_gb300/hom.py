@@ -36,8 +36,9 @@ HOM_FIELD_STRESS = 2
 HOM_KERNEL_PLANE_FWD = 0
 HOM_KERNEL_ZPASS = 1
 HOM_KERNEL_PLANE_INV = 2
-HOM_KERNEL_COUNT = 6
-KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64", "plane_inv_f64"]
+HOM_KERNEL_COUNT = 8
+KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64", "plane_inv_f64",
+                "ypass", "ypass_f64"]
 
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
             "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
@@ -48,7 +49,7 @@ class hom_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("scheme", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
                 ("l2_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("pass_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -245,7 +246,8 @@ class Homogenization:
     NLOADS = {0: 6, 1: 18, 2: 36}
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
-                 max_refine=6, rhs_chunk=0, l2_budget_bytes=64 << 20, stream=None, lam0=None, mu0=None):
+                 max_refine=6, rhs_chunk=0, l2_budget_bytes=64 << 20, stream=None, lam0=None, mu0=None,
+                 pass_mode=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
         self.M = n1 * n2 * n3
@@ -258,6 +260,7 @@ class Homogenization:
         opt.rhs_chunk = rhs_chunk
         opt.l2_budget_bytes = l2_budget_bytes
         opt.cuda_stream = stream
+        opt.pass_mode = pass_mode
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
                             ms.mu0 if mu0 is None else mu0, opt)
         self.nloads = {}

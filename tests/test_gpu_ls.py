@@ -26,9 +26,11 @@ def cases():
 CASES = list(cases())
 
 
+@pytest.mark.parametrize("pass_mode", [0, 2])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,ms", CASES, ids=[c[0] for c in CASES])
-def test_ls_step_matches_oracle(name, ms, precision):
+def test_ls_step_matches_oracle(name, ms, precision, pass_mode):
+    """Fused plane kernels (pass_mode 0 on these grids) and split x / y passes (pass_mode 2)."""
     from paper_1712_05145_gb300 import hom
     pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
     nrhs = 3
@@ -36,7 +38,7 @@ def test_ls_step_matches_oracle(name, ms, precision):
     rng = np.random.default_rng(5)
     E = rng.uniform(-1, 1, size=(nrhs, 6))
     ref = np.stack([oracle_ls_step_mandel(pb, eps[i], E[i]) for i in range(nrhs)])
-    H = hom.Homogenization(ms, precision=precision)
+    H = hom.Homogenization(ms, precision=precision, pass_mode=pass_mode)
     ed = torch.from_numpy(eps).cuda()
     out = torch.empty_like(ed)
     hom.hom_ls_apply(H.h, nrhs, ed, E, out)
@@ -63,3 +65,23 @@ def test_ls_step_chunking_gives_identical_results(precision):
         outs.append(o.cpu().numpy())
         H.close()
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_plane_larger_than_one_cta_uses_split_passes(precision):
+    """256 x 128 x 8: (N1/2) * N2 = 16384 complex values per plane, too many for one CTA."""
+    from paper_1712_05145_gb300 import hom
+    grid = (256, 128, 8)
+    ms = synthetic.Microstructure(random_phase(grid, 2, 9), np.array([[1.0, 1.0], [20.0, 12.0]]), 10.0, 6.0)
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    eps = random_mandel_fields(1, grid, 12)
+    E = np.array([[0.3, -0.2, 0.1, 0.5, 0.0, -0.4]])
+    ref = oracle_ls_step_mandel(pb, eps[0], E[0])
+    with pytest.raises(hom.HomError):
+        hom.Homogenization(ms, precision=precision, pass_mode=1)
+    H = hom.Homogenization(ms, precision=precision)
+    ed = torch.from_numpy(eps).cuda()
+    out = torch.empty_like(ed)
+    hom.hom_ls_apply(H.h, 1, ed, E, out)
+    assert rel_err(out.cpu().numpy()[0], ref) < TOL[precision]
+    H.close()

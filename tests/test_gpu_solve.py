@@ -68,8 +68,9 @@ def test_config_c1_laminate32_closed_form(precision, scheme):
     H.close()
 
 
+@pytest.mark.parametrize("pass_mode", [0, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_random_spheres_32_cg_vs_oracle(precision):
+def test_random_spheres_32_cg_vs_oracle(precision, pass_mode):
     from paper_1712_05145_gb300 import hom
     ms = synthetic.random_spheres((32, 32, 32), seed=3)
     pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
@@ -78,7 +79,7 @@ def test_random_spheres_32_cg_vs_oracle(precision):
     for a in loads:
         e, _, _ = pb.cg(pb.rhs(unit_mandel_load(a)), 1e-12)
         refs.append(tensor_to_mandel(e))
-    H = hom.Homogenization(ms, precision=precision, scheme=hom.HOM_CG)
+    H = hom.Homogenization(ms, precision=precision, scheme=hom.HOM_CG, pass_mode=pass_mode)
     info = H.solve(0, 1e-12 if precision == 0 else 1e-9)
     assert all(i["status"] == 0 for i in info), info
     for r, a in zip(refs, loads):
