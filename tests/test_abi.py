@@ -37,13 +37,26 @@ def test_status_strings_and_defaults(lib):
     assert o.precision == hom.HOM_FP32_REFINE and o.scheme == hom.HOM_CG and o.check_every == 8
 
 
-@pytest.mark.parametrize("grid", [(7, 8, 8), (10, 8, 8), (8, 5, 8), (8, 8, 10), (2, 8, 8), (1024, 32, 32)])
+@pytest.mark.parametrize("grid", [(7, 8, 8), (10, 8, 8), (8, 5, 8), (8, 8, 10), (2, 8, 8), (2048, 32, 32)])
 def test_unsupported_grids_rejected_before_any_cuda_call(lib, grid):
     n1, n2, n3 = grid
     phase = np.zeros((n3, n2, n1), dtype=np.uint8)
     with pytest.raises(hom.HomError) as e:
         hom.hom_create(grid, phase, np.array([[1.0, 1.0]]), 1.0, 1.0)
     assert e.value.status == hom.HOM_ERR_SIZE
+
+
+def test_fused_only_mode_rejects_planes_larger_than_one_cta(lib):
+    phase = np.zeros((8, 128, 256), dtype=np.uint8)
+    opt = hom.hom_default_options()
+    opt.pass_mode = 1
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_create((256, 128, 8), phase, np.array([[1.0, 1.0]]), 1.0, 1.0, opt)
+    assert e.value.status == hom.HOM_ERR_SIZE
+    opt.pass_mode = 3
+    with pytest.raises(hom.HomError) as e:
+        hom.hom_create((8, 8, 8), np.zeros((8, 8, 8), np.uint8), np.array([[1.0, 1.0]]), 1.0, 1.0, opt)
+    assert e.value.status == hom.HOM_ERR_ARG
 
 
 def test_bad_reference_medium_rejected(lib):
