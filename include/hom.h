@@ -179,6 +179,31 @@ HOM_API hom_status hom_profile(hom_t h, int32_t enable);
 /* Reads the counters into out[HOM_KERNEL_COUNT] (host array); synchronizes the stream. */
 HOM_API hom_status hom_profile_read(hom_t h, hom_kernel_stat* out);
 
+/* One Lippmann-Schwinger step without any device allocation, for callers that cannot allocate
+ * device memory: code that runs inside another library's memory pool or under an allocator it
+ * does not own, or a loop that must not call cudaMalloc.  The paper has no counterpart; this is
+ * the step of hom_ls_apply (FP64) with its scratch in a fixed device array of 16 MiB inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ *  grid, phase    as hom_create, but phase must be a device pointer (not copied).
+ *  n_phase, lame  as hom_create (lame is a host array); lambda0, mu0 the reference medium.
+ *  eps_in, eps_out device double [nrhs][6][N3][N2][N1] Mandel (eps_in NULL = zero field);
+ *                 E host double [nrhs][6] Mandel (NULL = zero); 1 <= nrhs <= 64.
+ *  cuda_stream    cudaStream_t the work is queued on (NULL = legacy default stream); the call
+ *                 returns once the work is queued, the result is ready when the stream is.
+ * Limit: the spectrum of one load, 96 * N3 * N2 * (N1/2 + 1) bytes, plus small tables must fit
+ * the 16 MiB (64^3 fits, 128 x 64 x 64 does not); larger grids return HOM_ERR_SIZE.
+ * The first call on a device resolves the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialized by the caller.
+ * Errors are described by hom_noalloc_last_error() (per host thread). */
+HOM_API hom_status hom_ls_apply_noalloc(const int32_t grid[3], const uint8_t* phase, int32_t n_phase,
+                                        const double* lame, double lambda0, double mu0, int32_t nrhs,
+                                        const double* eps_in, const double* E, double* eps_out,
+                                        void* cuda_stream);
+
+/* Text of the calling thread's last hom_ls_apply_noalloc error ("" after a success). */
+HOM_API const char* hom_noalloc_last_error(void);
+
 /* Bytes of device memory the handle holds now. */
 HOM_API int64_t hom_device_bytes(hom_t h);
 

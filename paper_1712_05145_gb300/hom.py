@@ -42,7 +42,8 @@ KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64",
 
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
             "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
-            "hom_profile_read", "hom_device_bytes", "hom_last_error", "hom_status_string", "hom_destroy"]
+            "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_device_bytes",
+            "hom_last_error", "hom_status_string", "hom_destroy"]
 
 
 class hom_options(ctypes.Structure):
@@ -109,6 +110,10 @@ def load_library(path=None):
     lib.hom_profile.restype = I32
     lib.hom_profile_read.argtypes = [V, V]
     lib.hom_profile_read.restype = I32
+    lib.hom_ls_apply_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int32), V, I32, V, D, D, I32, V, V, V, V]
+    lib.hom_ls_apply_noalloc.restype = I32
+    lib.hom_noalloc_last_error.argtypes = []
+    lib.hom_noalloc_last_error.restype = ctypes.c_char_p
     lib.hom_device_bytes.argtypes = [V]
     lib.hom_device_bytes.restype = I64
     lib.hom_last_error.argtypes = [V]
@@ -223,6 +228,23 @@ def hom_profile_read(h):
     _check(h, load_library().hom_profile_read(h, ctypes.cast(out, ctypes.c_void_p)))
     return [{"kernel": KERNEL_NAMES[k], "launches": out[k].launches, "bytes": out[k].bytes,
              "voxel_comps": out[k].voxel_comps, "ms": out[k].ms} for k in range(HOM_KERNEL_COUNT)]
+
+
+def hom_ls_apply_noalloc(grid, phase_dev, lame, lambda0, mu0, nrhs, eps_in, E, eps_out, stream=None):
+    """The allocation-free LS step (see include/hom.h); phase_dev, eps_in, eps_out on the device."""
+    lib = load_library()
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    lame = np.ascontiguousarray(lame, dtype=np.float64)
+    E = None if E is None else np.ascontiguousarray(E, dtype=np.float64).reshape(nrhs, 6)
+    s = lib.hom_ls_apply_noalloc(g, _ptr(phase_dev), int(lame.shape[0]), _ptr(lame), float(lambda0), float(mu0),
+                                 int(nrhs), _ptr(eps_in), _ptr(E), _ptr(eps_out), stream)
+    if s != HOM_OK:
+        raise HomError(s, lib.hom_noalloc_last_error().decode())
+    return eps_out
+
+
+def hom_noalloc_last_error():
+    return load_library().hom_noalloc_last_error().decode()
 
 
 def hom_device_bytes(h):
