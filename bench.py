@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--rhs-chunk", type=int, default=0,
+                    help="loads transformed per launch (0: as many as fit the spectrum budget)")
+    ap.add_argument("--l2-budget-mb", type=int, default=64, help="spectrum scratch budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -213,7 +216,8 @@ def main():
     M = ms.phase.size
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, scheme=hom.HOM_CG, stream=stream.cuda_stream)
+    H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, scheme=hom.HOM_CG, stream=stream.cuda_stream,
+                           rhs_chunk=args.rhs_chunk, l2_budget_bytes=args.l2_budget_mb << 20)
 
     def step():
         info = H.solve(0, TOL)
@@ -308,6 +312,7 @@ def main():
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [n, n, n], "loads": 6, "tol": TOL, "seed": SEED,
+                   "rhs_chunk": args.rhs_chunk, "l2_budget_mb": args.l2_budget_mb,
                    "l2": "inputs larger than L2 (x, r, p fields 302 MB each)", "parallelism": "replicas"},
         "solves_per_s": world * args.steps / (total_ms / 1e3),
         "p50_ms": float(np.percentile(step_ms, 50)),

@@ -48,6 +48,12 @@ __device__ __forceinline__ void st2(Tf* p, Tf a, Tf b) {
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Bulk prefetch of a contiguous global range into L2 (TMA, sm_90+).  bytes must be a multiple
+// of 16 and ptr 16-byte aligned; the range must lie inside one allocation.  Issued by one thread.
+__device__ __forceinline__ void prefetch_l2(const void* ptr, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
+}
+
 // Publishes this block's NQ totals (valid in thread 0 after block_sum_f64) and lets the
 // block that draws the last ticket sum all ncta partials in a fixed order.  Returns
 // true in that block, with the grand totals in thread 0's v.

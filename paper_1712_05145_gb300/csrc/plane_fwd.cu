@@ -26,6 +26,20 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
 
+  {
+    // start the plane's field reads now; they land in L2 while the tables load
+    const long long psz = (long long)n2 * n1;
+    const long long fo = ((long long)(rhs * a.in_ncomp + c) * g.n3 + z) * psz;
+    const unsigned pb = (unsigned)(psz * (long long)sizeof(Tf));
+    if (tid == 0 && (pb & 15u) == 0) {
+      if (a.mode == FWD_CG) {
+        prefetch_l2(a.r + fo, pb);
+        if (a.st[rhs].restart == 0) prefetch_l2(a.p + fo, pb);
+      } else if (a.in != nullptr) {
+        prefetch_l2(a.in + fo, pb);
+      }
+    }
+  }
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);

@@ -23,6 +23,23 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   int* flag = reinterpret_cast<int*>(sh + 64);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  {
+    // the epilogue's field planes are fetched into L2 while the transforms run
+    const long long psz = (long long)n2 * n1;
+    const unsigned pb = (unsigned)(psz * (long long)sizeof(Tf));
+    if (tid == 0 && (pb & 15u) == 0) {
+      if (a.mode == INV_CG) {
+        const long long fo = ((long long)(rhs * 6 + c) * g.n3 + z) * psz;
+        prefetch_l2(a.p + fo, pb);
+        prefetch_l2(a.x + fo, pb);
+        prefetch_l2(a.r + fo, pb);
+      } else {
+        const long long fo = ((long long)(rhs * a.out_ncomp + c) * g.n3 + z) * psz;
+        if (a.b != nullptr) prefetch_l2(a.b + fo, (unsigned)(psz * (long long)sizeof(double)));
+        if (a.fin == FIN_BASIC && a.prev != nullptr) prefetch_l2(a.prev + fo, pb);
+      }
+    }
+  }
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
