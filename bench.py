@@ -190,7 +190,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--rhs-chunk", type=int, default=0,
                     help="loads transformed per launch (0: as many as fit the spectrum budget)")
-    ap.add_argument("--l2-budget-mb", type=int, default=64, help="spectrum scratch budget")
+    ap.add_argument("--l2-budget-mb", type=int, default=128, help="spectrum scratch budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

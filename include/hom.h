@@ -69,7 +69,7 @@ typedef struct {
   int32_t max_refine;      /* FP32_REFINE: cap on FP64 residual-correction sweeps */
   int32_t rhs_chunk;       /* loads whose spectra are transformed per launch; 0 = choose so
                               that the spectrum scratch fits l2_budget_bytes */
-  int64_t l2_budget_bytes; /* target size of the spectrum scratch (0 = 64 MiB) */
+  int64_t l2_budget_bytes; /* target size of the spectrum scratch (0 = 128 MiB) */
   void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
   int32_t pass_mode;       /* x-y transforms: 0 = fused plane kernels when a plane fits one CTA,
                               else split x and y passes; 1 = always fused (fails if a plane does
@@ -87,7 +87,7 @@ typedef struct {
 } hom_solve_info;
 
 /* Fills *opt with defaults: HOM_FP32_REFINE, HOM_CG, max_iter 2000, check_every 8,
- * max_refine 6, rhs_chunk 0, l2_budget_bytes 64 MiB, own stream. */
+ * max_refine 6, rhs_chunk 0, l2_budget_bytes 128 MiB, own stream. */
 HOM_API void hom_default_options(hom_options* opt);
 
 /* Creates a handle for one voxel RVE (Sec. 2: C(x) piecewise isotropic, reference C0).
@@ -203,6 +203,56 @@ HOM_API hom_status hom_ls_apply_noalloc(const int32_t grid[3], const uint8_t* ph
 
 /* Text of the calling thread's last hom_ls_apply_noalloc error ("" after a success). */
 HOM_API const char* hom_noalloc_last_error(void);
+
+/* Device bytes a handle with default options needs to solve `order` (0 or 1) on this grid in
+ * `precision`, as counted from its allocations (used for admission by the server); -1 if the
+ * grid is not supported. */
+HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision);
+
+/* ---- request server: continuous batching of RVE solves (no counterpart in the paper) ----
+ * Requests are copied on submission and queued.  max_active worker threads, each with its own
+ * CUDA stream, admit queued requests first-fit against a device-memory budget (estimate above)
+ * as soon as a worker and enough memory are free; the kernels of admitted requests overlap on
+ * the device.  Each request runs hom_create / hom_solve (order 0, then order 1 if asked) /
+ * hom_effective / hom_destroy with default options of its precision and scheme, so its result
+ * is the same as when solved alone. */
+typedef struct hom_server_ctx* hom_server_t;
+
+typedef struct {
+  int32_t grid[3];
+  const uint8_t* phase;    /* host [N3][N2][N1], copied at submission */
+  int32_t n_phase;
+  const double* lame;      /* host [n_phase][2], copied */
+  double lambda0, mu0;
+  int32_t order;           /* 0 or 1 (order 1 also solves order 0) */
+  int32_t precision;       /* HOM_FP32_REFINE or HOM_FP64 */
+  int32_t scheme;          /* HOM_CG or HOM_BASIC */
+  int32_t reserved;
+  double tol;
+} hom_request;
+
+typedef struct {
+  int32_t done;            /* 0 while queued or running */
+  int32_t status;          /* hom_status of the solve */
+  int32_t iterations;      /* CG / fixed-point iterations summed over all loads */
+  int32_t order;
+  double queue_ms, run_ms, latency_ms;  /* submission -> start -> end (host steady clock) */
+  double c_eff[36];        /* 6x6 Mandel, row-major */
+  double d1[108];          /* 6x18 Mandel (order 1) */
+} hom_result;
+
+/* budget_bytes <= 0: 85 % of the free device memory at creation.  1 <= max_active <= 64. */
+HOM_API hom_status hom_server_create(int64_t budget_bytes, int32_t max_active, hom_server_t* out);
+/* Queues a request; *id identifies it.  HOM_ERR_NOMEM if it can never fit the budget. */
+HOM_API hom_status hom_server_submit(hom_server_t s, const hom_request* req, int64_t* id);
+/* Copies the result if the request is done (out->done = 1), else sets out->done = 0. */
+HOM_API hom_status hom_server_poll(hom_server_t s, int64_t id, hom_result* out);
+/* Blocks until the request is done, then copies its result. */
+HOM_API hom_status hom_server_wait(hom_server_t s, int64_t id, hom_result* out);
+/* Queue length, running requests and the estimated bytes they hold (each pointer nullable). */
+HOM_API hom_status hom_server_stats(hom_server_t s, int64_t* queued, int64_t* running, int64_t* bytes_in_use);
+/* Waits for every queued and running request, then releases the server. */
+HOM_API void hom_server_destroy(hom_server_t s);
 
 /* Bytes of device memory the handle holds now. */
 HOM_API int64_t hom_device_bytes(hom_t h);

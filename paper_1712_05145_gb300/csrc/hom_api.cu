@@ -457,6 +457,11 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   // the FP64 residual they restart from.
   const double kSweepGain = 1e-5, kFirstSweepFloor = 3e-7;
   const double tol_inner = (mixed && !basic) ? std::max(0.5 * tol, kFirstSweepFloor) : (mixed ? 0.5 * tol : tol);
+  // The FP32 corrections leave incompatible rounding noise in x of ~1e-7 relative; it enters the
+  // FP64 residual at that level.  Below tol 1e-6 the residual sweeps therefore run on the
+  // projected x (one more FP64 pass per sweep); at looser tolerances the noise is under tol/10.
+  const double kProjectBelow = 1e-6;
+  const bool project = mixed && tol < kProjectBelow;
 
   std::vector<RhsState> st(n);
   for (int i = 0; i < n; ++i) {
@@ -526,7 +531,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
     for (int i = 0; i < n; ++i) st[i].active = 1;
     CKS(write_states(c, st));
     std::vector<int> all(n, 1);
-    if (mixed) CKS(project_compatible(c, n, x64, &all));
+    if (project) CKS(project_compatible(c, n, x64, &all));
     CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &all));
     CKS(read_states(c, n, st));
     for (int i = 0; i < n; ++i) {
@@ -600,7 +605,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
       }
       if (!need) break;
       CKS(write_states(c, st));
-      if (mixed) CKS(project_compatible(c, n, x64, &act));
+      if (project) CKS(project_compatible(c, n, x64, &act));
       CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       CKS(read_states(c, n, st));
       bool again = false;
@@ -857,7 +862,7 @@ HOM_API void hom_default_options(hom_options* opt) {
   opt->check_every = 8;
   opt->max_refine = 6;
   opt->rhs_chunk = 0;
-  opt->l2_budget_bytes = 64LL << 20;
+  opt->l2_budget_bytes = 128LL << 20;
   opt->cuda_stream = nullptr;
 }
 
@@ -879,6 +884,38 @@ HOM_API const char* hom_status_string(hom_status s) {
 HOM_API const char* hom_last_error(hom_t h) { return h ? h->err.c_str() : "null handle"; }
 
 HOM_API int64_t hom_device_bytes(hom_t h) { return h ? (int64_t)h->bytes : 0; }
+
+HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision) {
+  if (!grid) return -1;
+  const long long n1 = grid[0], n2 = grid[1], n3 = grid[2];
+  if (n1 < 4 || (n1 & 1) || !fft_length_supported((int)(n1 / 2)) || !fft_length_supported((int)n2) ||
+      !fft_length_supported((int)n3) || order < 0 || order > 2)
+    return -1;
+  const bool fp32 = (precision == HOM_FP32_REFINE);
+  const long long M = n1 * n2 * n3, plane_c = n2 * (n1 / 2 + 1);
+  const long long budget = 128LL << 20;
+  auto scratch = [&](long long elem) {
+    const long long per = 6 * n3 * plane_c * elem;
+    long long chunk = std::max(1LL, budget / per);
+    chunk = std::min(chunk, 64LL);
+    return per / 6 * std::max(6 * chunk, 9LL);
+  };
+  long long b = M + (1LL << 20);                 // phase, tables, states
+  b += scratch(fp32 ? 8 : 16);
+  if (fp32) b += scratch(16);
+  const long long nl = order >= 1 ? (order == 2 ? 36 : 18) : 6, tf = fp32 ? 4 : 8;
+  b += 2 * nl * 6 * M * tf;                      // r, p
+  long long slot3 = fp32 ? nl * 6 * M * 4 : 0;   // FP32 correction d
+  if (order >= 1) {
+    b += nl * 6 * M * 8;                         // right-hand sides
+    slot3 = std::max(slot3, nl * 9 * M * 8);     // p and g of the right-hand-side build
+  }
+  b += slot3;
+  b += 6 * 9 * M * 8;                            // order-0 strain and displacement
+  if (order >= 1) b += 18 * 15 * M * 8;          // order-1 strain, displacement, polarization
+  if (order >= 2) b += 36 * 15 * M * 8;
+  return (int64_t)((double)b * 1.05) + (16LL << 20);
+}
 
 HOM_API hom_status hom_profile(hom_t c, int32_t enable) {
   if (!c) return HOM_ERR_ARG;
@@ -946,7 +983,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if (c->opt.max_iter < 1) c->opt.max_iter = 1;
   if (c->opt.check_every < 1) c->opt.check_every = 1;
   if (c->opt.max_refine < 0) c->opt.max_refine = 0;
-  if (c->opt.l2_budget_bytes <= 0) c->opt.l2_budget_bytes = 64LL << 20;
+  if (c->opt.l2_budget_bytes <= 0) c->opt.l2_budget_bytes = 128LL << 20;
   if (c->opt.precision != HOM_FP64 && c->opt.precision != HOM_FP32_REFINE) { delete c; return HOM_ERR_ARG; }
   if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG) { delete c; return HOM_ERR_ARG; }
   c->fp32 = (c->opt.precision == HOM_FP32_REFINE);

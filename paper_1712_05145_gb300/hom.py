@@ -42,8 +42,9 @@ KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64",
 
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
             "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
-            "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_device_bytes",
-            "hom_last_error", "hom_status_string", "hom_destroy"]
+            "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
+            "hom_server_create", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
+            "hom_server_destroy", "hom_device_bytes", "hom_last_error", "hom_status_string", "hom_destroy"]
 
 
 class hom_options(ctypes.Structure):
@@ -66,6 +67,25 @@ class hom_solve_info(ctypes.Structure):
 class hom_kernel_stat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("bytes", ctypes.c_int64), ("voxel_comps", ctypes.c_int64),
                 ("ms", ctypes.c_double)]
+
+
+class hom_request(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32 * 3), ("phase", ctypes.c_void_p), ("n_phase", ctypes.c_int32),
+                ("lame", ctypes.c_void_p), ("lambda0", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("order", ctypes.c_int32), ("precision", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class hom_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("c_eff", ctypes.c_double * 36), ("d1", ctypes.c_double * 108)]
+
+    def as_dict(self):
+        return {"done": self.done, "status": self.status, "iterations": self.iterations, "order": self.order,
+                "queue_ms": self.queue_ms, "run_ms": self.run_ms, "latency_ms": self.latency_ms,
+                "c_eff": np.array(self.c_eff[:]).reshape(6, 6),
+                "d1": np.array(self.d1[:]).reshape(6, 18) if self.order >= 1 else None}
 
 
 class HomError(RuntimeError):
@@ -114,6 +134,20 @@ def load_library(path=None):
     lib.hom_ls_apply_noalloc.restype = I32
     lib.hom_noalloc_last_error.argtypes = []
     lib.hom_noalloc_last_error.restype = ctypes.c_char_p
+    lib.hom_estimate_bytes.argtypes = [ctypes.POINTER(ctypes.c_int32), I32, I32]
+    lib.hom_estimate_bytes.restype = I64
+    lib.hom_server_create.argtypes = [I64, I32, ctypes.POINTER(V)]
+    lib.hom_server_create.restype = I32
+    lib.hom_server_submit.argtypes = [V, ctypes.POINTER(hom_request), ctypes.POINTER(I64)]
+    lib.hom_server_submit.restype = I32
+    lib.hom_server_poll.argtypes = [V, I64, ctypes.POINTER(hom_result)]
+    lib.hom_server_poll.restype = I32
+    lib.hom_server_wait.argtypes = [V, I64, ctypes.POINTER(hom_result)]
+    lib.hom_server_wait.restype = I32
+    lib.hom_server_stats.argtypes = [V, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.hom_server_stats.restype = I32
+    lib.hom_server_destroy.argtypes = [V]
+    lib.hom_server_destroy.restype = None
     lib.hom_device_bytes.argtypes = [V]
     lib.hom_device_bytes.restype = I64
     lib.hom_last_error.argtypes = [V]
@@ -247,6 +281,61 @@ def hom_noalloc_last_error():
     return load_library().hom_noalloc_last_error().decode()
 
 
+def hom_estimate_bytes(grid, order, precision=HOM_FP32_REFINE):
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    return int(load_library().hom_estimate_bytes(g, int(order), int(precision)))
+
+
+def hom_server_create(budget_bytes=0, max_active=4):
+    s = ctypes.c_void_p()
+    st = load_library().hom_server_create(int(budget_bytes), int(max_active), ctypes.byref(s))
+    if st != HOM_OK:
+        raise HomError(st, "hom_server_create")
+    return s
+
+
+def hom_server_submit(s, ms, order=0, tol=1e-6, precision=HOM_FP32_REFINE, scheme=HOM_CG):
+    """Queues the RVE ``ms`` (a synthetic.Microstructure); returns the request id."""
+    n3, n2, n1 = ms.phase.shape
+    phase = np.ascontiguousarray(ms.phase, dtype=np.uint8)
+    lame = np.ascontiguousarray(ms.lame, dtype=np.float64)
+    q = hom_request()
+    q.grid[:] = [n1, n2, n3]
+    q.phase = phase.ctypes.data
+    q.n_phase = lame.shape[0]
+    q.lame = lame.ctypes.data
+    q.lambda0, q.mu0 = float(ms.lam0), float(ms.mu0)
+    q.order, q.precision, q.scheme, q.tol = int(order), int(precision), int(scheme), float(tol)
+    rid = ctypes.c_int64()
+    st = load_library().hom_server_submit(s, ctypes.byref(q), ctypes.byref(rid))
+    if st != HOM_OK:
+        raise HomError(st, "hom_server_submit")
+    return rid.value
+
+
+def hom_server_poll(s, rid):
+    r = hom_result()
+    _check(None, load_library().hom_server_poll(s, int(rid), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def hom_server_wait(s, rid):
+    r = hom_result()
+    _check(None, load_library().hom_server_wait(s, int(rid), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def hom_server_stats(s):
+    q, r, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(None, load_library().hom_server_stats(s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)))
+    return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
+
+
+def hom_server_destroy(s):
+    if s:
+        load_library().hom_server_destroy(s)
+
+
 def hom_device_bytes(h):
     return int(load_library().hom_device_bytes(h))
 
@@ -268,7 +357,7 @@ class Homogenization:
     NLOADS = {0: 6, 1: 18, 2: 36}
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
-                 max_refine=6, rhs_chunk=0, l2_budget_bytes=64 << 20, stream=None, lam0=None, mu0=None,
+                 max_refine=6, rhs_chunk=0, l2_budget_bytes=128 << 20, stream=None, lam0=None, mu0=None,
                  pass_mode=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
