@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
       const long long f = f0 + tc;
       if (f >= g.plane_c) continue;
       int kx, ky;
-      if (f < nmain) { ky = (int)(f / g.h); kx = (int)(f - (long long)ky * g.h); }
+      if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
       else { ky = (int)(f - nmain); kx = g.h; }
       // discrete wave vector: Nyquist components taken as 0
       const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);

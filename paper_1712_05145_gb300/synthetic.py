@@ -266,6 +266,56 @@ def voronoi(grid=(128, 128, 128), seed=1716, n_grains=256, sigma=1.0, nu_range=(
     return Microstructure(phase, lame, lam0, mu0, "voronoi", {"seed": seed, "n_grains": n_grains})
 
 
+def voronoi_seeds(grid, seed, n_grains, sigma=1.0, nu_range=(0.2, 0.4)):
+    """Seeds (unit-cell coordinates) and Lame table of ``voronoi``, without voxelising."""
+    rng = Xoshiro256ss(seed)
+    lengths = _cell_lengths(grid)
+    seeds = np.array([[rng.uniform(-0.5 * lengths[a], 0.5 * lengths[a]) for a in range(3)]
+                      for _ in range(n_grains)])
+    lame = []
+    for _ in range(n_grains):
+        e = math.exp(sigma * rng.normal())
+        nu = rng.uniform(*nu_range)
+        lame.append(lame_from_young(e, nu))
+    return seeds, np.array(lame)
+
+
+def voronoi_torch(grid=(512, 512, 512), seed=1716, n_grains=256, device="cuda"):
+    """The tessellation of ``voronoi`` voxelised with torch (FP64, nearest seed under the periodic
+    minimum image), for grids too large for the numpy loop.  Same seeds, tables and distance."""
+    import torch
+    seeds, lame = voronoi_seeds(grid, seed, n_grains)
+    lengths = _cell_lengths(grid)
+    n1, n2, n3 = grid
+    y1, y2, y3 = voxel_centres(grid)
+    c = [torch.tensor(y - (-0.5) - 0.5 * L, dtype=torch.float64, device=device)
+         for y, L in zip((y1, y2, y3), lengths)]
+    sd = torch.tensor(seeds, dtype=torch.float64, device=device)
+    Lt = torch.tensor(lengths, dtype=torch.float64, device=device)
+    phase = torch.empty((n3, n2, n1), dtype=torch.uint8, device=device)
+
+    def wrap(d, L):
+        return d - L * torch.round(d / L)
+    d1 = wrap(c[0][None, :] - sd[:, 0:1], Lt[0]) ** 2          # (G, n1)
+    d2 = wrap(c[1][None, :] - sd[:, 1:2], Lt[1]) ** 2          # (G, n2)
+    for z0 in range(0, n3, 32):
+        z1 = min(n3, z0 + 32)
+        d3 = wrap(c[2][None, z0:z1] - sd[:, 2:3], Lt[2]) ** 2  # (G, nz)
+        best = None
+        for g in range(n_grains):
+            dist = d3[g][:, None, None] + d2[g][None, :, None] + d1[g][None, None, :]
+            if best is None:
+                best = dist
+                lab = torch.zeros_like(dist, dtype=torch.uint8)
+            else:
+                better = dist < best
+                best = torch.where(better, dist, best)
+                lab = torch.where(better, torch.tensor(g, dtype=torch.uint8, device=device), lab)
+        phase[z0:z1] = lab
+    lam0, mu0 = midpoint_reference(lame)
+    return Microstructure(phase, lame, lam0, mu0, "voronoi", {"seed": seed, "n_grains": n_grains})
+
+
 def coated_sphere(n=32, r1=0.25, r2=0.4, e_core=100.0, e_coat=1000.0, e_matrix=453.685, nu=0.3):
     """Centred coated sphere: core r < r1, coating r1 <= r < r2, matrix outside."""
     y1, y2, y3 = voxel_centres((n, n, n))
