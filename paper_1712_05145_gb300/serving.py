@@ -85,6 +85,9 @@ def main():
     res, wall = run_stream(reqs, rate, args.max_active, args.tol, args.seed)
     lat = np.array([r["latency_ms"] for r in res])
     ok = sum(1 for r in res if r["status"] == 0)
+    failed = [{"grid": list(reqs[i][0].grid), "order": reqs[i][1], "contrast": reqs[i][0].meta["contrast"],
+               "status": res[i]["status"], "iterations": res[i]["iterations"]}
+              for i in range(len(res)) if res[i]["status"] != 0]
     # plain FP64, one solve after the other, on the first baseline requests
     nb = min(args.baseline_requests, len(reqs))
     t0 = time.perf_counter()
@@ -103,7 +106,7 @@ def main():
            "solves_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "mean_run_ms": float(np.mean([r["run_ms"] for r in res])),
            "fp64_sequential": {"requests": nb, "seconds": fp64_s, "solves_per_s": nb / fp64_s},
-           "served_run_seconds_same_requests": served_sub}
+           "served_run_seconds_same_requests": served_sub, "failed": failed[:20]}
     print(json.dumps(out), flush=True)
 
 
