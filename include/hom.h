@@ -92,8 +92,11 @@ HOM_API void hom_default_options(hom_options* opt);
 
 /* Creates a handle for one voxel RVE (Sec. 2: C(x) piecewise isotropic, reference C0).
  *  grid[3]     N1, N2, N3.  N1 even with N1/2, N2 and N3 in {2,3,4,6,8,12,16,24,32,48,64,96,
- *              128,192,256,384,512}.  Planes with (N1/2) * N2 <= 8192 can use the fused plane
- *              kernels; larger ones use split x and y passes (hom_options.pass_mode).
+ *              128,192,256,384,512}; N3 may also be 1, a two-dimensional cell (every field is
+ *              constant along y3 and xi3 = 0: plane strain, or plane stress with the plane-stress
+ *              Lame parameter 2 lambda mu / (lambda + 2 mu) in place of lambda).  Planes with
+ *              (N1/2) * N2 <= 8192 can use the fused plane kernels; larger ones use split x and y
+ *              passes (hom_options.pass_mode).
  *  phase       uint8 [N3][N2][N1], host or device pointer (auto-detected); copied.
  *  n_phase     1..256; every phase index must be < n_phase.
  *  lame        double [n_phase][2] host array of (lambda, mu) per phase; copied.
@@ -110,8 +113,11 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
  * Basic Scheme this is the paper's Cauchy quantity ||eps_{n+1} - eps_n|| / ||eps_0||.
  *  order 0: n_loads macroscopic strains, loads = double [n_loads][6] Mandel host array, or
  *           loads = NULL for the 6 unit loads (n_loads ignored).  n_loads <= 64.
- *  order 1: requires a converged order 0 with unit loads; loads must be NULL (18 loads).
- *  order 2: requires order 1; loads must be NULL (36 loads).
+ *  order 1: loads = NULL for the 18 unit loads grad E = E^A (x) e_k (load 3A+k, A the Mandel
+ *           component, k the direction), or loads = double [n_loads][18] host array of
+ *           coefficients of those unit loads (n_loads <= 64), each solved as one system.
+ *           Every unit load used needs the unit strain e_A among the converged order-0 loads.
+ *  order 2: requires order 1 solved for its 18 unit loads; loads must be NULL (36 loads).
  *  info     host array of one hom_solve_info per load (nullable); caller-owned.
  * The correctors stay on the device, owned by the handle, until hom_destroy or the next
  * solve of the same order.  Returns HOM_ERR_NOT_CONVERGED if any load missed tol. */
@@ -120,7 +126,8 @@ HOM_API hom_status hom_solve(hom_t h, int32_t order, int32_t n_loads, const doub
 
 /* Effective tensors as FP64 voxel means of the stress of each load (host array out):
  *  order 0: 6 x n_loads, column A = <C : (E^A + eps^A)> (the 6x6 C_eff for unit loads);
- *  order 1: 6 x 18, column = <C : eps_2 + p_2> (mean order-2 stress of the paper's alpha=2);
+ *  order 1: 6 x n_loads (18 for the unit loads), column = <C : eps_2 + p_2> (mean order-2
+ *           stress of the paper's alpha = 2);
  *  order 2: 6 x 36, column = <C : eps_3 + p_3>. */
 HOM_API hom_status hom_effective(hom_t h, int32_t order, double* out);
 
@@ -239,6 +246,7 @@ typedef struct {
   double queue_ms, run_ms, latency_ms;  /* submission -> start -> end (host steady clock) */
   double c_eff[36];        /* 6x6 Mandel, row-major */
   double d1[108];          /* 6x18 Mandel (order 1) */
+  char message[160];       /* hom_last_error text of a failed request, "" on success */
 } hom_result;
 
 /* budget_bytes <= 0: 85 % of the free device memory at creation.  1 <= max_active <= 64. */
@@ -256,6 +264,10 @@ HOM_API void hom_server_destroy(hom_server_t s);
 
 /* Bytes of device memory the handle holds now. */
 HOM_API int64_t hom_device_bytes(hom_t h);
+
+/* Kernels this library has launched in this process so far, over all handles, servers and the
+ * allocation-free entry point (a host-side count of launches issued, not of launches finished). */
+HOM_API int64_t hom_launch_count(void);
 
 /* Text of the last error on this handle ("" if none); valid until the next call. */
 HOM_API const char* hom_last_error(hom_t h);

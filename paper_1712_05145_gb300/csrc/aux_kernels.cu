@@ -79,20 +79,24 @@ static int grid_for(long long n, int threads) {
 
 template <typename Tf>
 cudaError_t launch_mandel_to_kelvin(const double* in, Tf* out, long long M, int nf, cudaStream_t s) {
+  count_launch();
   mandel_to_kelvin_kernel<Tf><<<grid_for(M * nf, 256), 256, 0, s>>>(in, out, M, nf);
   return cudaGetLastError();
 }
 template <typename Tf>
 cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int nf, cudaStream_t s) {
+  count_launch();
   kelvin_to_mandel_kernel<Tf><<<grid_for(M * nf, 256), 256, 0, s>>>(in, out, M, nf);
   return cudaGetLastError();
 }
 cudaError_t launch_kelvin_to_mandel_inplace(double* f, long long M, int nf, cudaStream_t s) {
+  count_launch();
   kelvin_to_mandel_inplace_kernel<<<grid_for(M * nf, 256), 256, 0, s>>>(f, M, nf);
   return cudaGetLastError();
 }
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long long n, cudaStream_t s) {
+  count_launch();
   convert_kernel<Ti, To><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
@@ -103,6 +107,7 @@ __global__ void add_correction_kernel(const float* __restrict__ d, double* __res
     x[i] += (double)d[i];
 }
 cudaError_t launch_add_correction(const float* d, double* x, long long n, cudaStream_t s) {
+  count_launch();
   add_correction_kernel<<<grid_for(n, 256), 256, 0, s>>>(d, x, n);
   return cudaGetLastError();
 }
@@ -197,6 +202,7 @@ template <typename T>
 cudaError_t launch_spec_from_std(const double* in, cx<T>* S, const Geo& g, int nf, int ncomp, int basis,
                                  cudaStream_t s) {
   const long long n = (long long)nf * g.n3 * g.n2 * (g.h + 1);
+  count_launch();
   spec_from_std_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(in, S, g, nf, ncomp, basis);
   return cudaGetLastError();
 }
@@ -204,6 +210,7 @@ template <typename T>
 cudaError_t launch_spec_to_std(const cx<T>* S, double* out, const Geo& g, int nf, int ncomp, int basis,
                                cudaStream_t s) {
   const long long n = (long long)nf * g.n3 * g.n2 * (g.h + 1);
+  count_launch();
   spec_to_std_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(S, out, g, nf, ncomp, basis);
   return cudaGetLastError();
 }
@@ -247,9 +254,11 @@ cudaError_t launch_weighted_mean(const Tf* f, int ncomp, int nrhs, const double*
                                  const double* mat, int wsel, long long M, double* part, int nblk, double* out,
                                  cudaStream_t s) {
   dim3 g1(nblk, ncomp, nrhs);
+  count_launch();
   mean_partial_kernel<Tf><<<g1, 256, 0, s>>>(f, ncomp, shift, phase, mat, wsel, M, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  count_launch();
   mean_final_kernel<<<nrhs * ncomp, 256, 0, s>>>(part, nblk, M, out);
   return cudaGetLastError();
 }

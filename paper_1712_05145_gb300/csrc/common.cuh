@@ -269,12 +269,14 @@ struct StageSeq<T, DIR, EPT, N, NS, R, Rs...> {
   }
 };
 
-// Axis lengths the kernels accept (host side checks with fft_length_supported).
+// Axis lengths the kernels accept (host side checks with fft_length_supported).  The z axis may
+// also have length 1 (a two-dimensional cell, see z_length_supported).
 __host__ __device__ constexpr bool fft_length_supported(int n) {
   return n == 2 || n == 3 || n == 4 || n == 6 || n == 8 || n == 12 || n == 16 || n == 24 ||
          n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 ||
          n == 384 || n == 512;
 }
+__host__ __device__ constexpr bool z_length_supported(int n) { return n == 1 || fft_length_supported(n); }
 
 // Runs the FFT of length n on `npen` pencils (npd divides by npen).  EPT bounds elements per
 // thread: the caller guarantees npen * n <= EPT * blockDim.x.
@@ -284,6 +286,7 @@ __device__ __forceinline__ void fft_pencils(cx<T>* buf, const Addr& addr, int n,
 #define HOM_SEQ(NN, ...) \
   case NN: StageSeq<T, DIR, EPT, NN, 1, __VA_ARGS__>::run(buf, addr, npen, npd, tw); break;
   switch (n) {
+    case 1: break;  // a single plane along z (two-dimensional cells): the transform is the identity
     HOM_SEQ(2, 2)
     HOM_SEQ(3, 3)
     HOM_SEQ(4, 4)

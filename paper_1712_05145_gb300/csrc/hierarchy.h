@@ -12,10 +12,20 @@ namespace hom {
 //  order 2 (paper alpha = 3), load 6A+P, (k,l) the P-th Mandel pair, w = 1/(1+d_kl):
 //          p = C : w [sym(u^(A,k) (x) e_l) + sym(u^(A,l) (x) e_k)],
 //          g_i = w [s^(A,k)_il + s^(A,l)_ik],  s = C : eps_2 + p_2  from the order-1 correctors.
+//  For order 1, map selects the loads: load L is the unit load u = map.unit[L] = 3A+k, and the
+//  order-0 correctors of E^A are those of order-0 load map.a0[A].
+struct UnitMap {
+  int unit[18];
+  int a0[6];
+};
 template <typename Tf>
-cudaError_t launch_rhs_pointwise(int order, int nload, const Tf* disp, const Tf* eps, const Tf* pprev,
-                                 const double* EK, const uint8_t* phase, const double* mat, long long M,
-                                 Tf* out9, Tf* pf, cudaStream_t s);
+cudaError_t launch_rhs_pointwise(int order, int nload, const UnitMap& map, const Tf* disp, const Tf* eps,
+                                 const Tf* pprev, const double* EK, const uint8_t* phase, const double* mat,
+                                 long long M, Tf* out9, Tf* pf, cudaStream_t s);
+
+// out[l][i] = sum_u W[l][u] in[u][i] for l < nout, u < nin, i < per (linear combinations of loads).
+cudaError_t launch_combine_loads(const double* in, int nin, const double* W, int nout, long long per, double* out,
+                                 cudaStream_t s);
 
 // Mandel stress of one load: C : (eps + E) (EK non-null) or C : eps + p (pf non-null).
 template <typename Tf>

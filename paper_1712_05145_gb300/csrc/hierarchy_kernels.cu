@@ -43,7 +43,8 @@ __device__ __forceinline__ void add_sym_vec_dir(double* t, const double* v, int 
 }
 
 template <typename Tf>
-__global__ void rhs_pointwise_kernel(int order, int nload, const Tf* __restrict__ disp, const Tf* __restrict__ eps,
+__global__ void rhs_pointwise_kernel(int order, int nload, const UnitMap map, const Tf* __restrict__ disp,
+                                     const Tf* __restrict__ eps,
                                      const Tf* __restrict__ pprev, const double* __restrict__ EK,
                                      const uint8_t* __restrict__ phase, const double* __restrict__ mat, long long M,
                                      Tf* __restrict__ out9, Tf* __restrict__ pf) {
@@ -56,7 +57,7 @@ __global__ void rhs_pointwise_kernel(int order, int nload, const Tf* __restrict_
     const double ch = mat[ph * 4 + 2], cd = mat[ph * 4 + 3];
     double t[6] = {0, 0, 0, 0, 0, 0}, g[3];
     if (order == 1) {
-      const int A = L / 3, k = L - 3 * (L / 3);
+      const int u = map.unit[L], k = u % 3, A = map.a0[u / 3];
       double chi[3];
       for (int i = 0; i < 3; ++i) chi[i] = (double)disp[((long long)A * 3 + i) * M + v];
       add_sym_vec_dir(t, chi, k, 1.0);
@@ -129,26 +130,49 @@ static int blocks_for(long long n) {
 }
 
 template <typename Tf>
-cudaError_t launch_rhs_pointwise(int order, int nload, const Tf* disp, const Tf* eps, const Tf* pprev,
-                                 const double* EK, const uint8_t* phase, const double* mat, long long M,
-                                 Tf* out9, Tf* pf, cudaStream_t s) {
-  rhs_pointwise_kernel<Tf><<<blocks_for((long long)nload * M), 256, 0, s>>>(order, nload, disp, eps, pprev, EK,
-                                                                             phase, mat, M, out9, pf);
+cudaError_t launch_rhs_pointwise(int order, int nload, const UnitMap& map, const Tf* disp, const Tf* eps,
+                                 const Tf* pprev, const double* EK, const uint8_t* phase, const double* mat,
+                                 long long M, Tf* out9, Tf* pf, cudaStream_t s) {
+  count_launch();
+  rhs_pointwise_kernel<Tf><<<blocks_for((long long)nload * M), 256, 0, s>>>(order, nload, map, disp, eps, pprev,
+                                                                             EK, phase, mat, M, out9, pf);
+  return cudaGetLastError();
+}
+
+__global__ void combine_loads_kernel(const double* __restrict__ in, int nin, const double* __restrict__ W, int nout,
+                                     long long per, double* __restrict__ out) {
+  const long long total = (long long)nout * per;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(id / per);
+    const long long i = id - (long long)l * per;
+    double acc = 0.0;
+    for (int u = 0; u < nin; ++u) acc += W[l * nin + u] * in[(long long)u * per + i];
+    out[id] = acc;
+  }
+}
+
+cudaError_t launch_combine_loads(const double* in, int nin, const double* W, int nout, long long per, double* out,
+                                 cudaStream_t s) {
+  count_launch();
+  combine_loads_kernel<<<blocks_for((long long)nout * per), 256, 0, s>>>(in, nin, W, nout, per, out);
   return cudaGetLastError();
 }
 
 template <typename Tf>
 cudaError_t launch_stress_field(const Tf* eps, const double* EK, const Tf* pf, const uint8_t* phase,
                                 const double* mat, long long M, double* out, cudaStream_t s) {
+  count_launch();
   stress_kernel<Tf><<<blocks_for(M), 256, 0, s>>>(eps, EK, pf, phase, mat, M, out);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_rhs_pointwise<float>(int, int, const float*, const float*, const float*, const double*,
-                                                 const uint8_t*, const double*, long long, float*, float*, cudaStream_t);
-template cudaError_t launch_rhs_pointwise<double>(int, int, const double*, const double*, const double*,
-                                                  const double*, const uint8_t*, const double*, long long, double*,
-                                                  double*, cudaStream_t);
+template cudaError_t launch_rhs_pointwise<float>(int, int, const UnitMap&, const float*, const float*, const float*,
+                                                 const double*, const uint8_t*, const double*, long long, float*,
+                                                 float*, cudaStream_t);
+template cudaError_t launch_rhs_pointwise<double>(int, int, const UnitMap&, const double*, const double*,
+                                                  const double*, const double*, const uint8_t*, const double*,
+                                                  long long, double*, double*, cudaStream_t);
 template cudaError_t launch_stress_field<float>(const float*, const double*, const float*, const uint8_t*,
                                                 const double*, long long, double*, cudaStream_t);
 template cudaError_t launch_stress_field<double>(const double*, const double*, const double*, const uint8_t*,

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -20,6 +21,14 @@
 #include "internal.h"
 
 using namespace hom;
+
+namespace hom {
+std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> n{0};
+  return n;
+}
+void count_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
+}  // namespace hom
 
 namespace {
 
@@ -54,6 +63,7 @@ struct OrderData {
   void* pf = nullptr;     // Tf [nloads][6][M] Kelvin polarization p_alpha (orders >= 1)
   std::vector<double> loadsK;  // order 0: [nloads][6] Kelvin macroscopic strains
   std::vector<double> eff;     // [6][nloads] Mandel mean stresses
+  bool unit = true;            // orders >= 1: the loads are the unit loads (not combinations)
 };
 
 struct hom_ctx {
@@ -728,8 +738,11 @@ hom_status displacements(hom_ctx* c, int order) {
 
 // Right-hand sides b = -Gamma0 * (p_alpha + theta_alpha) of order 1 or 2 (Sec. 3, modified
 // initialization), in FP64, with p_alpha kept in pf for the effective tensor.
-hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf) {
-  const int n = (order == 1) ? 18 : 36;
+// Right-hand sides of order `order` (b = -Gamma0 * (p + theta), Sec. 3) and the polarizations p:
+// order 1 for the nu unit loads map.unit[0..nu) (order-0 correctors through map.a0), order 2 for
+// the 36 unit loads.
+hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf, const UnitMap& map, int nu) {
+  const int n = (order == 1) ? nu : 36;
   CKS(displacements(c, order - 1));
   const OrderData& lo = c->ord[order - 1];
   void* v9;
@@ -737,8 +750,9 @@ hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf) {
   double* f9 = reinterpret_cast<double*>(v9);
   CKS(ensure_cap(c, std::max(n, 6)));
   if (order == 1)
-    CK(cudaMemcpyAsync(c->d_E, c->ord[0].loadsK.data(), sizeof(double) * 36, cudaMemcpyHostToDevice, c->stream));
-  CK(launch_rhs_pointwise<double>(order, n, reinterpret_cast<const double*>(lo.disp),
+    CK(cudaMemcpyAsync(c->d_E, c->ord[0].loadsK.data(), sizeof(double) * c->ord[0].loadsK.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  CK(launch_rhs_pointwise<double>(order, n, map, reinterpret_cast<const double*>(lo.disp),
                                   reinterpret_cast<const double*>(lo.eps),
                                   order == 2 ? reinterpret_cast<const double*>(lo.pf) : nullptr, c->d_E, c->d_phase,
                                   c->d_mat64, c->g.M, f9, pf, c->stream));
@@ -810,18 +824,88 @@ hom_status solve_order0(hom_ctx* c, int n, const double* loads, double tol, hom_
   return s;
 }
 
+// order-0 load index holding the unit Mandel strain e_A, for each A (-1 if none)
+void unit_order0_loads(const hom_ctx* c, int a0[6]) {
+  const OrderData& o = c->ord[0];
+  for (int A = 0; A < 6; ++A) a0[A] = -1;
+  for (int i = 0; i < o.nloads; ++i) {
+    double m[6];
+    kelvin_to_mandel6(&o.loadsK[i * 6], m);
+    for (int A = 0; A < 6; ++A) {
+      bool unit = true;
+      for (int j = 0; j < 6; ++j) unit = unit && std::fabs(m[j] - (j == A ? 1.0 : 0.0)) < 1e-14;
+      if (unit && a0[A] < 0) a0[A] = i;
+    }
+  }
+}
+
+// Order 1 or 2 (the paper's alpha = 2, 3).  Order 1 solves the 18 unit loads (W = NULL) or n
+// combinations of them, W [n][18]; order 2 solves its 36 unit loads from the 18 unit loads of
+// order 1.
 template <typename Tf>
-hom_status solve_higher(hom_ctx* c, int order, double tol, hom_solve_info* info) {
-  const int n = (order == 1) ? 18 : 36;
-  if (!c->ord[order - 1].solved || (order == 1 && c->ord[0].nloads != 6))
-    return fail(c, HOM_ERR_ORDER, "order %d needs a converged order %d with unit loads", order, order - 1);
+hom_status solve_higher(hom_ctx* c, int order, int n, const double* W, double tol, hom_solve_info* info) {
+  if (!c->ord[order - 1].solved) return fail(c, HOM_ERR_ORDER, "order %d needs a converged order %d", order, order - 1);
+  UnitMap map{};
+  int nu = 0;
+  std::vector<double> Wu;  // W restricted to the unit loads used, [n][nu]
+  if (order == 1) {
+    int a0[6];
+    unit_order0_loads(c, a0);
+    for (int u = 0; u < 18; ++u) {
+      bool used = (W == nullptr);
+      for (int l = 0; l < n && !used; ++l) used = (W[l * 18 + u] != 0.0);
+      if (!used) continue;
+      if (a0[u / 3] < 0)
+        return fail(c, HOM_ERR_ORDER, "order-1 load (A=%d, k=%d) needs the unit order-0 load e_%d", u / 3, u % 3,
+                    u / 3);
+      map.unit[nu++] = u;
+    }
+    for (int A = 0; A < 6; ++A) map.a0[A] = a0[A] < 0 ? 0 : a0[A];
+    if (nu == 0) return fail(c, HOM_ERR_ARG, "every order-1 load is zero");
+    if (W != nullptr) {
+      Wu.assign((size_t)n * nu, 0.0);
+      for (int l = 0; l < n; ++l)
+        for (int j = 0; j < nu; ++j) Wu[(size_t)l * nu + j] = W[l * 18 + map.unit[j]];
+    }
+  } else if (!c->ord[1].unit) {
+    return fail(c, HOM_ERR_ORDER, "order 2 needs order 1 solved for its 18 unit loads");
+  }
   CKS(alloc_order(c, order, n, true));
   OrderData& o = c->ord[order];
   o.solved = false;
+  o.unit = (W == nullptr);
   void* vb;
   CKS(work(c, 2, tbytes<double>(c, n, 6), &vb));
   double* b = reinterpret_cast<double*>(vb);
-  CKS(build_rhs(c, order, b, reinterpret_cast<double*>(o.pf)));
+  if (order == 1 && W != nullptr) {
+    // the unit right-hand sides and polarizations, then their combinations (both linear in the load)
+    void *bu = nullptr, *pu = nullptr, *dW = nullptr;
+    const size_t ub = tbytes<double>(c, nu, 6);
+    hom_status st = dalloc(c, &bu, ub);
+    if (st == HOM_OK) st = dalloc(c, &pu, ub);
+    if (st == HOM_OK) st = dalloc(c, &dW, sizeof(double) * Wu.size());
+    if (st == HOM_OK) st = build_rhs(c, 1, reinterpret_cast<double*>(bu), reinterpret_cast<double*>(pu), map, nu);
+    if (st == HOM_OK &&
+        cudaMemcpyAsync(dW, Wu.data(), sizeof(double) * Wu.size(), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      st = fail(c, HOM_ERR_CUDA, "copy of the load combinations failed");
+    const long long per = 6LL * c->g.M;
+    if (st == HOM_OK && launch_combine_loads(reinterpret_cast<const double*>(bu), nu,
+                                             reinterpret_cast<const double*>(dW), n, per, b,
+                                             c->stream) != cudaSuccess)
+      st = fail(c, HOM_ERR_CUDA, "combine_loads launch failed");
+    if (st == HOM_OK && launch_combine_loads(reinterpret_cast<const double*>(pu), nu,
+                                             reinterpret_cast<const double*>(dW), n, per,
+                                             reinterpret_cast<double*>(o.pf), c->stream) != cudaSuccess)
+      st = fail(c, HOM_ERR_CUDA, "combine_loads launch failed");
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess && st == HOM_OK)
+      st = fail(c, HOM_ERR_CUDA, "building the order-1 combinations failed");
+    if (bu) dfree(c, bu, ub);
+    if (pu) dfree(c, pu, ub);
+    if (dW) dfree(c, dW, sizeof(double) * Wu.size());
+    if (st != HOM_OK) return st;
+  } else {
+    CKS(build_rhs(c, order, b, reinterpret_cast<double*>(o.pf), map, order == 1 ? nu : 36));
+  }
   hom_status s = solve_system<Tf>(c, n, nullptr, b, reinterpret_cast<double*>(o.eps), tol, info);
   if (s != HOM_OK && s != HOM_ERR_NOT_CONVERGED) return s;
   CKS(mean_stress(c, order, o.eff));
@@ -885,11 +969,13 @@ HOM_API const char* hom_last_error(hom_t h) { return h ? h->err.c_str() : "null 
 
 HOM_API int64_t hom_device_bytes(hom_t h) { return h ? (int64_t)h->bytes : 0; }
 
+HOM_API int64_t hom_launch_count(void) { return hom::launch_counter().load(std::memory_order_relaxed); }
+
 HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision) {
   if (!grid) return -1;
   const long long n1 = grid[0], n2 = grid[1], n3 = grid[2];
   if (n1 < 4 || (n1 & 1) || !fft_length_supported((int)(n1 / 2)) || !fft_length_supported((int)n2) ||
-      !fft_length_supported((int)n3) || order < 0 || order > 2)
+      !z_length_supported((int)n3) || order < 0 || order > 2)
     return -1;
   const bool fp32 = (precision == HOM_FP32_REFINE);
   const long long M = n1 * n2 * n3, plane_c = n2 * (n1 / 2 + 1);
@@ -971,7 +1057,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     return HOM_ERR_ARG;
   const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
   if (n1 < 4 || (n1 & 1) || !fft_length_supported(n1 / 2) || !fft_length_supported(n2) ||
-      !fft_length_supported(n3))
+      !z_length_supported(n3))
     return HOM_ERR_SIZE;
   const int pass_mode = opt ? opt->pass_mode : 0;
   if (pass_mode < 0 || pass_mode > 2) return HOM_ERR_ARG;
@@ -1101,23 +1187,16 @@ HOM_API hom_status hom_solve(hom_t c, int32_t order, int32_t n_loads, const doub
     for (int k = order + 1; k < 3; ++k) c->ord[k].solved = false;
     return c->fp32 ? solve_order0<float>(c, n, loads, tol, info) : solve_order0<double>(c, n, loads, tol, info);
   }
-  if (loads) return fail(c, HOM_ERR_ARG, "orders 1 and 2 take only the unit loads (loads = NULL)");
-  if (order == 1) {
-    const std::vector<double>& L = c->ord[0].loadsK;
-    bool unit = c->ord[0].nloads == 6;
-    if (unit) {
-      for (int i = 0; i < 6 && unit; ++i) {
-        double m[6];
-        kelvin_to_mandel6(&L[i * 6], m);
-        for (int j = 0; j < 6; ++j) unit = unit && std::fabs(m[j] - (i == j ? 1.0 : 0.0)) < 1e-14;
-      }
-    }
-    if (!unit || !c->ord[0].solved) return fail(c, HOM_ERR_ORDER, "order 1 needs order 0 solved for the unit loads");
+  if (order == 2 && loads) return fail(c, HOM_ERR_ARG, "order 2 takes only its unit loads (loads = NULL)");
+  int n = (order == 1) ? 18 : 36;
+  if (order == 1 && loads) {
+    n = n_loads;
+    if (n < 1 || n > 64) return fail(c, HOM_ERR_ARG, "n_loads must be in 1..64");
   }
-  if (order == 2 && !c->ord[1].solved) return fail(c, HOM_ERR_ORDER, "order 2 needs order 1 solved");
   c->ord[order].solved = false;
   if (order == 1) c->ord[2].solved = false;
-  return c->fp32 ? solve_higher<float>(c, order, tol, info) : solve_higher<double>(c, order, tol, info);
+  return c->fp32 ? solve_higher<float>(c, order, n, loads, tol, info)
+                 : solve_higher<double>(c, order, n, loads, tol, info);
 }
 
 HOM_API hom_status hom_effective(hom_t c, int32_t order, double* out) {

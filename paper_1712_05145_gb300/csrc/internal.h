@@ -149,4 +149,7 @@ void geo_finish(Geo& g);
 template <typename T>
 void zpass_tiling(ZArgs<T>& a);
 
+// counts one kernel launch of this library (process-wide; read by hom_launch_count)
+void count_launch();
+
 }  // namespace hom

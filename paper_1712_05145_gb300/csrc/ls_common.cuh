@@ -19,6 +19,9 @@
 namespace hom {
 
 constexpr int kEPT = 16;
+// elements per thread whose global loads a plane kernel issues together in its prologue and
+// epilogue loops
+constexpr int kBatch = 4;
 // A CG sweep whose residual has not halved for kStallIters iterations ends (the FP64
 // residual sweep then restarts it, or reports non-convergence).  Below kNearFloor (relative
 // residual) an FP32 sweep is close to its rounding floor and a shorter window applies.
@@ -143,15 +146,30 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
 }
 
 // Dynamic shared memory above 48 KB needs an opt-in; the carveout asks for the largest shared
-// memory partition so that the occupancy is not limited by a small default carveout.
+// memory partition so that the occupancy is not limited by a small default carveout.  The
+// opt-in is a per-function, per-context limit shared by every host thread, so it is always set
+// to the device maximum rather than to this launch's size: with per-launch values, a thread
+// launching a small grid could lower the limit between another thread's set and its launch.
+// The limit only bounds a launch; occupancy follows the bytes each launch asks for.
+inline int smem_optin_max() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return v;
+}
+
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  if (bytes > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaSuccess;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  const int optin = smem_optin_max();
+  if ((long long)bytes > optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 }  // namespace hom

@@ -78,23 +78,43 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
       }
     }
   } else if (a.mode == FWD_CG) {
+    // Flat element index e = row * h + col; the loads of kBatch elements per thread are issued
+    // before the first store of p (which the compiler must assume may alias r).
     const RhsState& s = a.st[rhs];
     const bool restart = (s.restart != 0);
     const T beta = restart ? (T)0 : (T)s.beta;
-    #pragma unroll 4
-    for (int row = warp; row < n2; row += nwarp) {
-      for (int c2 = lane; c2 < h; c2 += 32) {
-        const long long o = (long long)row * n1 + 2 * c2;
-        Tf r0, r1, p0 = 0, p1 = 0;
-        ld2<Tf>(a.r + foff + o, r0, r1);
-        if (!restart) ld2<Tf>(a.p + foff + o, p0, p1);   // a restart never reads the old p
-        const T q0 = (T)r0 + beta * (T)p0;
-        const T q1 = (T)r1 + beta * (T)p1;
-        st2<Tf>(a.p + foff + o, (Tf)q0, (Tf)q1);
-        const uchar2 ph = *reinterpret_cast<const uchar2*>(php + o);
-        const T c0 = tab[a.n_phase + ph.x], c1 = tab[a.n_phase + ph.y];
-        acc += c0 * q0 * q0 + c1 * q1 * q1;
-        pl[row * P + c2] = mk<T>(c0 * q0, c1 * q1);
+    const Tf* rp = a.r + foff;
+    Tf* pp = a.p + foff;
+    const int total = n2 * h;
+    for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
+      Tf r0[kBatch], r1[kBatch], p0[kBatch], p1[kBatch];
+      uchar2 ph[kBatch];
+      int rw[kBatch];
+      #pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        rw[j] = (int)g.fd_h.div((unsigned)e);
+        p0[j] = 0;
+        p1[j] = 0;
+        if (e < total) {
+          const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
+          ld2<Tf>(rp + o, r0[j], r1[j]);
+          if (!restart) ld2<Tf>(pp + o, p0[j], p1[j]);   // a restart never reads the old p
+          ph[j] = *reinterpret_cast<const uchar2*>(php + o);
+        }
+      }
+      #pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        if (e < total) {
+          const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
+          const T q0 = (T)r0[j] + beta * (T)p0[j];
+          const T q1 = (T)r1[j] + beta * (T)p1[j];
+          st2<Tf>(pp + o, (Tf)q0, (Tf)q1);
+          const T c0 = tab[a.n_phase + ph[j].x], c1 = tab[a.n_phase + ph[j].y];
+          acc += c0 * q0 * q0 + c1 * q1 * q1;
+          pl[rw[j] * P + col] = mk<T>(c0 * q0, c1 * q1);
+        }
       }
     }
   } else {  // FWD_COPY, FWD_C0
@@ -166,9 +186,11 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
   __syncthreads();
 
   cx<T>* Sp = a.S + ((long long)(lrhs * a.ncomp + c) * g.n3 + z) * g.plane_c;
-  #pragma unroll 4
-  for (int row = warp; row < n2; row += nwarp)
-    for (int col = lane; col < h; col += 32) Sp[(long long)row * h + col] = pl[row * P + col];
+  // the spectrum plane is contiguous (row pitch h): flat index e = row * h + col
+  for (int e = tid; e < n2 * h; e += nthr) {
+    const int row = (int)g.fd_h.div((unsigned)e);
+    Sp[e] = pl[row * P + (e - row * h)];
+  }
   for (int ky = tid; ky < n2; ky += nthr) Sp[(long long)n2 * h + ky] = nyq[ky];
 
   if (a.mode == FWD_CG) {
@@ -257,6 +279,7 @@ cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.n3, a.ncomp, nrhs);
+  count_launch();
   k<<<grid, a.g.thr_plane, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -53,16 +53,27 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)psz);
   }
-  const long long nmain = (long long)n2 * h;
-  #pragma unroll 4
-  for (int row = warp; row < n2; row += nwarp) {
-    for (int col = lane; col < h; col += 32) {
-      cx<T> v = Sp[(long long)row * h + col];
-      if (col == 0) {  // pack kx = 0 (A) and kx = n1/2 (B) as A + i B
-        const cx<T> b = Sp[nmain + row];
-        v = mk<T>(v.re - b.im, v.im + b.re);
+  const int nmain = n2 * h;
+  // the spectrum plane is contiguous (row pitch h): flat index e = row * h + col, loads of
+  // kBatch elements per thread in flight together
+  for (int e0 = tid; e0 < nmain; e0 += kBatch * nthr) {
+    cx<T> v[kBatch];
+    #pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const int e = e0 + j * nthr;
+      if (e < nmain) v[j] = Sp[e];
+    }
+    #pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const int e = e0 + j * nthr;
+      if (e < nmain) {
+        const int row = (int)g.fd_h.div((unsigned)e), col = e - row * h;
+        if (col == 0) {  // pack kx = 0 (A) and kx = n1/2 (B) as A + i B
+          const cx<T> b = Sp[nmain + row];
+          v[j] = mk<T>(v[j].re - b.im, v[j].im + b.re);
+        }
+        pl[row * P + col] = v[j];
       }
-      pl[row * P + col] = v;
     }
   }
   __syncthreads();
@@ -121,24 +132,43 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
       }
     }
   } else {  // INV_CG: q = A p = Gamma0 * (C : p) = -eta, x += alpha p, r -= alpha q
+    // Flat element index e = row * h + col; each thread issues the loads of kBatch elements
+    // before the first store, so that they are in flight together (the stores to x and r
+    // may alias p for the compiler, which would otherwise serialise load -> store chains).
     const long long foff = ((long long)(rhs * 6 + c) * g.n3 + z) * plane_sz;
     const T alpha = (T)a.st[rhs].alpha;
     const T cw = (c == 0) ? c0h : c0d;
-    #pragma unroll 4
-    for (int row = warp; row < n2; row += nwarp) {
-      for (int c2 = lane; c2 < h; c2 += 32) {
-        const long long o = foff + (long long)row * n1 + 2 * c2;
-        const cx<T> e = pl[row * P + c2];
-        Tf p0, p1, x0, x1, r0, r1;
-        ld2<Tf>(a.p + o, p0, p1);
-        ld2<Tf>(a.x + o, x0, x1);
-        ld2<Tf>(a.r + o, r0, r1);
-        const T xa = (T)x0 + alpha * (T)p0, xb = (T)x1 + alpha * (T)p1;
-        const T ra = (T)r0 + alpha * e.re, rb = (T)r1 + alpha * e.im;
-        st2<Tf>(a.x + o, (Tf)xa, (Tf)xb);
-        st2<Tf>(a.r + o, (Tf)ra, (Tf)rb);
-        q0 += cw * (ra * ra + rb * rb);
-        q1 += ra * ra + rb * rb;
+    const Tf* pp = a.p + foff;
+    Tf* xp = a.x + foff;
+    Tf* rp = a.r + foff;
+    const int total = n2 * h;
+    for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
+      Tf p0[kBatch], p1[kBatch], x0[kBatch], x1[kBatch], r0[kBatch], r1[kBatch];
+      int rw[kBatch];
+      #pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        rw[j] = (int)g.fd_h.div((unsigned)e);
+        if (e < total) {
+          const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
+          ld2<Tf>(pp + o, p0[j], p1[j]);
+          ld2<Tf>(xp + o, x0[j], x1[j]);
+          ld2<Tf>(rp + o, r0[j], r1[j]);
+        }
+      }
+      #pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        if (e < total) {
+          const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
+          const cx<T> v = pl[rw[j] * P + col];
+          const T xa = (T)x0[j] + alpha * (T)p0[j], xb = (T)x1[j] + alpha * (T)p1[j];
+          const T ra = (T)r0[j] + alpha * v.re, rb = (T)r1[j] + alpha * v.im;
+          st2<Tf>(xp + o, (Tf)xa, (Tf)xb);
+          st2<Tf>(rp + o, (Tf)ra, (Tf)rb);
+          q0 += cw * (ra * ra + rb * rb);
+          q1 += ra * ra + rb * rb;
+        }
       }
     }
   }
@@ -163,6 +193,7 @@ cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.n3, a.ncomp, nrhs);
+  count_launch();
   k<<<grid, a.g.thr_plane, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -89,7 +90,7 @@ void run_request(ServerRequest* r, cudaStream_t stream) {
   r->phase.shrink_to_fit();
   int iters = 0;
   if (st == HOM_OK) {
-    hom_solve_info info[18];
+    hom_solve_info info[18] = {};
     st = hom_solve(h, 0, 6, nullptr, r->tol, info);
     for (int i = 0; i < 6; ++i) iters += info[i].iterations;
     if (st == HOM_OK) st = hom_effective(h, 0, res.c_eff);
@@ -98,6 +99,10 @@ void run_request(ServerRequest* r, cudaStream_t stream) {
       for (int i = 0; i < 18; ++i) iters += info[i].iterations;
       if (st == HOM_OK) st = hom_effective(h, 1, res.d1);
     }
+  }
+  if (st != HOM_OK) {
+    const char* m = h ? hom_last_error(h) : hom_status_string(st);
+    std::snprintf(res.message, sizeof(res.message), "%s", m ? m : "");
   }
   if (h) hom_destroy(h);
   res.status = st;

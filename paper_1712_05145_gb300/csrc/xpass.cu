@@ -272,6 +272,7 @@ cudaError_t launch_xpass_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.nrb, a.ncomp, nrhs);
+  count_launch();
   k<<<grid, a.g.thr_x, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -284,6 +285,7 @@ cudaError_t launch_xpass_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.nrb, a.ncomp, nrhs);
+  count_launch();
   k<<<grid, a.g.thr_x, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -76,11 +76,13 @@ cudaError_t launch_ypass(const cx<T>* tw_n2, cx<T>* S, const Geo& g, int ncomp, 
     auto k = ypass_kernel<T, -1, kEPT>;
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
+    count_launch();
     k<<<grid, g.thr_y, smem, s>>>(tw_n2, S, g, ncomp, s_ncomp, prof, st, rhs0);
   } else {
     auto k = ypass_kernel<T, +1, kEPT>;
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
+    count_launch();
     k<<<grid, g.thr_y, smem, s>>>(tw_n2, S, g, ncomp, s_ncomp, prof, st, rhs0);
   }
   return cudaGetLastError();

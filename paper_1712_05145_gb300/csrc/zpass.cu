@@ -167,6 +167,7 @@ cudaError_t launch_zpass(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.ntiles, nrhs);
+  count_launch();
   k<<<grid, a.nthr, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -44,7 +44,8 @@ EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "
             "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
             "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
             "hom_server_create", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
-            "hom_server_destroy", "hom_device_bytes", "hom_last_error", "hom_status_string", "hom_destroy"]
+            "hom_server_destroy", "hom_device_bytes", "hom_launch_count", "hom_last_error", "hom_status_string",
+            "hom_destroy"]
 
 
 class hom_options(ctypes.Structure):
@@ -79,13 +80,15 @@ class hom_request(ctypes.Structure):
 class hom_result(ctypes.Structure):
     _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double), ("c_eff", ctypes.c_double * 36), ("d1", ctypes.c_double * 108)]
+                ("latency_ms", ctypes.c_double), ("c_eff", ctypes.c_double * 36), ("d1", ctypes.c_double * 108),
+                ("message", ctypes.c_char * 160)]
 
     def as_dict(self):
         return {"done": self.done, "status": self.status, "iterations": self.iterations, "order": self.order,
                 "queue_ms": self.queue_ms, "run_ms": self.run_ms, "latency_ms": self.latency_ms,
                 "c_eff": np.array(self.c_eff[:]).reshape(6, 6),
-                "d1": np.array(self.d1[:]).reshape(6, 18) if self.order >= 1 else None}
+                "d1": np.array(self.d1[:]).reshape(6, 18) if self.order >= 1 else None,
+                "message": self.message.decode(errors="replace")}
 
 
 class HomError(RuntimeError):
@@ -150,6 +153,8 @@ def load_library(path=None):
     lib.hom_server_destroy.restype = None
     lib.hom_device_bytes.argtypes = [V]
     lib.hom_device_bytes.restype = I64
+    lib.hom_launch_count.argtypes = []
+    lib.hom_launch_count.restype = I64
     lib.hom_last_error.argtypes = [V]
     lib.hom_last_error.restype = ctypes.c_char_p
     lib.hom_status_string.argtypes = [I32]
@@ -212,7 +217,7 @@ def hom_solve(h, order, tol, loads=None):
     nl = {0: 6, 1: 18, 2: 36}[order] if loads is None else int(np.asarray(loads).shape[0])
     arr = None
     if loads is not None:
-        arr = np.ascontiguousarray(loads, dtype=np.float64).reshape(nl, 6)
+        arr = np.ascontiguousarray(loads, dtype=np.float64).reshape(nl, 6 if order == 0 else 18)
     info = (hom_solve_info * nl)()
     s = lib.hom_solve(h, int(order), nl, _ptr(arr), float(tol), ctypes.cast(info, ctypes.c_void_p))
     if s not in (HOM_OK, HOM_ERR_NOT_CONVERGED):
@@ -338,6 +343,11 @@ def hom_server_destroy(s):
 
 def hom_device_bytes(h):
     return int(load_library().hom_device_bytes(h))
+
+
+def hom_launch_count():
+    """Kernels the library has launched in this process (host-side count)."""
+    return int(load_library().hom_launch_count())
 
 
 def hom_last_error(h):

@@ -86,7 +86,8 @@ def main():
     lat = np.array([r["latency_ms"] for r in res])
     ok = sum(1 for r in res if r["status"] == 0)
     failed = [{"grid": list(reqs[i][0].grid), "order": reqs[i][1], "contrast": reqs[i][0].meta["contrast"],
-               "status": res[i]["status"], "iterations": res[i]["iterations"]}
+               "status": res[i]["status"], "iterations": res[i]["iterations"],
+               "message": res[i]["message"]}
               for i in range(len(res)) if res[i]["status"] != 0]
     # plain FP64, one solve after the other, on the first baseline requests
     nb = min(args.baseline_requests, len(reqs))

@@ -76,3 +76,23 @@ def test_admission_respects_the_memory_budget():
         hom.hom_server_submit(s, big, 1, 1e-6)
     assert e.value.status == hom.HOM_ERR_NOMEM
     hom.hom_server_destroy(s)
+
+
+def test_concurrent_requests_with_different_plane_sizes():
+    """Workers that run grids with different shared-memory needs at once (x-y planes of 64 KB and
+    96 KB per CTA) all succeed and give the result of the solo solve."""
+    from paper_1712_05145_gb300 import hom
+    tol = 1e-6
+    grids = [(128, 128, 8), (192, 128, 8), (128, 128, 12), (192, 128, 6)]
+    reqs = [(synthetic.random_spheres(g, seed=20 + i, inclusion_e=50.0), i % 2) for i, g in enumerate(grids)]
+    ref = [solo(ms, order, tol) for ms, order in reqs]
+    s = hom.hom_server_create(0, 6)
+    ids = [hom.hom_server_submit(s, ms, order, tol) for _ in range(3) for ms, order in reqs]
+    res = [hom.hom_server_wait(s, i) for i in ids]
+    hom.hom_server_destroy(s)
+    for k, r in enumerate(res):
+        assert r["status"] == 0, r["message"]
+        c, d = ref[k % len(reqs)]
+        np.testing.assert_allclose(r["c_eff"], c, rtol=0, atol=1e-12 * np.abs(c).max())
+        if d is not None:
+            np.testing.assert_allclose(r["d1"], d, rtol=0, atol=1e-12 * max(np.abs(d).max(), 1e-30))
