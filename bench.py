@@ -242,6 +242,7 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     iters = 0
     per_step_iters = []
+    per_step_refine = []
     launches0 = hom.hom_launch_count()
     ev[0].record(stream)
     for k in range(args.steps):
@@ -249,6 +250,7 @@ def main():
         it = sum(i["iterations"] for i in info)
         iters += it
         per_step_iters.append(it)
+        per_step_refine.append([i["refinements"] for i in info])
         ev[k + 1].record(stream)
     barrier()
     n_launches = hom.hom_launch_count() - launches0
@@ -319,6 +321,9 @@ def main():
         "p50_ms": float(np.percentile(step_ms, 50)),
         "p99_ms": float(np.percentile(step_ms, 99)),
         "cg_iterations_per_step": per_step_iters,
+        "fp64_refinements_per_load": per_step_refine[-1],
+        "per_load": [{"iterations": i["iterations"], "rel_residual": i["rel_residual"],
+                      "rel_residual_fp64": i["rel_residual_fp64"]} for i in info],
         "rel_residual_fp64_max": max(worst),
         "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -57,13 +57,16 @@ typedef enum {
 } hom_status;
 
 enum { HOM_FP64 = 0, HOM_FP32_REFINE = 1 };
-enum { HOM_BASIC = 0, HOM_CG = 1 };
+enum { HOM_BASIC = 0, HOM_CG = 1, HOM_BICGSTAB = 2 };
 enum { HOM_FIELD_STRAIN = 0, HOM_FIELD_DISPLACEMENT = 1, HOM_FIELD_STRESS = 2 };
 
 typedef struct {
   int32_t precision;       /* HOM_FP64: FP64 fields and FFTs.  HOM_FP32_REFINE: FP32 fields and
                               FFTs, FP64 reductions, FP64 residual-correction sweeps. */
-  int32_t scheme;          /* HOM_BASIC (fixed point) or HOM_CG (CG on A eps = b, C0 product) */
+  int32_t scheme;          /* HOM_BASIC (fixed point), HOM_CG (CG on A eps = b, C0 product) or
+                              HOM_BICGSTAB (BiCGSTAB on A eps = b, L2 products; the solver the
+                              paper ran for its CG-version, Sec. 4; iterations count full steps,
+                              each with two operator applications) */
   int32_t max_iter;        /* iteration cap per load (inner iterations in FP32_REFINE) */
   int32_t check_every;     /* iterations between host convergence checks (>= 1) */
   int32_t max_refine;      /* FP32_REFINE: cap on FP64 residual-correction sweeps */
@@ -233,7 +236,7 @@ typedef struct {
   double lambda0, mu0;
   int32_t order;           /* 0 or 1 (order 1 also solves order 0) */
   int32_t precision;       /* HOM_FP32_REFINE or HOM_FP64 */
-  int32_t scheme;          /* HOM_CG or HOM_BASIC */
+  int32_t scheme;          /* HOM_CG, HOM_BASIC or HOM_BICGSTAB */
   int32_t reserved;
   double tol;
 } hom_request;

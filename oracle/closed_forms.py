@@ -13,6 +13,11 @@ Lippmann-Schwinger solution must reproduce or respect:
 * ``voigt`` / ``reuss`` -- arithmetic mean of C and harmonic mean of C.
 * ``hs_bulk_bounds`` -- Hashin-Shtrikman bounds on the bulk modulus of a two-phase
   composite of isotropic phases.
+* ``coated_cylinder_bulk`` / ``hashin_neutral_matrix_young`` -- Hashin's coated-cylinder
+  assemblage (the structure of Sec. 4): its in-plane bulk modulus, and the matrix modulus that
+  makes a coated inclusion neutral.  A neutral coated inclusion leaves a uniform hydrostatic
+  field in the matrix undisturbed, so under in-plane hydrostatic strain the periodic cell of
+  Sec. 4 has the matrix bulk modulus exactly (in the continuum).
 """
 import numpy as np
 
@@ -77,3 +82,38 @@ def hs_bulk_bounds(phase1, phase2, f2):
 def effective_bulk(c_eff):
     """Bulk modulus of a 6x6 Mandel stiffness under hydrostatic strain: (1/9) sum C_ij, i,j<3."""
     return float(np.sum(c_eff[:3, :3]) / 9.0)
+
+
+def plane_stress_moduli(e, nu):
+    """In-plane bulk and shear moduli of an isotropic plate in plane stress:
+    kappa = E / (2 (1 - nu)) (mean in-plane stress over the trace of the in-plane strain) and
+    mu = E / (2 (1 + nu))."""
+    return e / (2.0 * (1.0 - nu)), e / (2.0 * (1.0 + nu))
+
+
+def coated_cylinder_bulk(k_core, k_coat, mu_coat, f):
+    """In-plane bulk modulus of Hashin's coated-cylinder assemblage with core fraction f (of the
+    coated cylinder): kappa* = k2 + f / (1 / (k1 - k2) + (1 - f) / (k2 + mu2)), the classical
+    composite-cylinder result in terms of two-dimensional bulk moduli."""
+    return k_coat + f / (1.0 / (k_core - k_coat) + (1.0 - f) / (k_coat + mu_coat))
+
+
+def hashin_neutral_matrix_young(e_core, e_coat, r1, r2, nu, plane_stress=True):
+    """Young's modulus of the matrix that makes the coated disk (core r < r1, coating r < r2,
+    common Poisson ratio nu) of Sec. 4 neutral: its two-dimensional bulk modulus equals the
+    coated-cylinder bulk modulus with f = (r1 / r2)^2."""
+    f = (r1 / r2) ** 2
+    if plane_stress:
+        k1, _ = plane_stress_moduli(e_core, nu)
+        k2, mu2 = plane_stress_moduli(e_coat, nu)
+        return 2.0 * (1.0 - nu) * coated_cylinder_bulk(k1, k2, mu2, f)
+    # plane strain: kappa = lambda + mu = E / (2 (1 + nu) (1 - 2 nu))
+    kp = lambda e: e / (2.0 * (1.0 + nu) * (1.0 - 2.0 * nu))
+    mu2 = e_coat / (2.0 * (1.0 + nu))
+    return 2.0 * (1.0 + nu) * (1.0 - 2.0 * nu) * coated_cylinder_bulk(kp(e_core), kp(e_coat), mu2, f)
+
+
+def in_plane_bulk(c_eff):
+    """In-plane bulk modulus (C11 + C22 + 2 C12) / 4 of a 6x6 Mandel stiffness (mean in-plane
+    stress per unit in-plane trace under in-plane hydrostatic strain)."""
+    return 0.25 * (c_eff[0, 0] + c_eff[1, 1] + c_eff[0, 1] + c_eff[1, 0])

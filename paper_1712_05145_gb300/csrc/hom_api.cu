@@ -97,6 +97,8 @@ struct hom_ctx {
   double* d_mout = nullptr;
   int mblk = 64;
   void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t
+  size_t bicg_bytes = 0;
   size_t work_bytes[4] = {0, 0, 0, 0};
   OrderData ord[3];
   size_t bytes = 0;
@@ -442,6 +444,72 @@ hom_status residual_sweep(hom_ctx* c, int n, const double* dE, const double* b64
   return ls_pass<double, Tf, double>(c, n, fa, za, ia, act);
 }
 
+// out = A in = Gamma0 * (C : in) for compatible in (Eq. cg_form), one LS pass with the sign of
+// eta reversed; loads whose device state is inactive are skipped.
+template <typename Tf>
+hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<int>* act) {
+  auto fa = fwd_args<Tf, Tf>(c, FWD_STRESS, 6, 6);
+  fa.in = in;
+  fa.st = c->d_st;
+  auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
+  za.st = c->d_st;
+  auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 6, 6, 6);
+  ia.out = out;
+  ia.out_scale = (Tf)-1;
+  ia.st = c->d_st;
+  return ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia, act);
+}
+
+// One BiCGSTAB sweep on A x = r from the current x (FP64 mode: the solution; FP32 mode: the
+// correction d), until every load's device state is inactive.
+template <typename Tf>
+hom_status bicgstab_sweep(hom_ctx* c, int n, Tf* x, Tf* r, Tf* p, std::vector<RhsState>& st, std::vector<int>& act) {
+  const size_t fb = tbytes<Tf>(c, n, 6);
+  if (c->bicg_bytes < 4 * fb) {
+    if (c->d_bicg) dfree(c, c->d_bicg, c->bicg_bytes);
+    c->d_bicg = nullptr;
+    c->bicg_bytes = 0;
+    CKS(dalloc(c, &c->d_bicg, 4 * fb));
+    c->bicg_bytes = 4 * fb;
+  }
+  char* w = reinterpret_cast<char*>(c->d_bicg);
+  BicgArgs<Tf> a;
+  a.x = x;
+  a.r = r;
+  a.p = p;
+  a.rh = reinterpret_cast<Tf*>(w);
+  a.v = reinterpret_cast<Tf*>(w + fb);
+  a.s = reinterpret_cast<Tf*>(w + 2 * fb);
+  a.t = reinterpret_cast<Tf*>(w + 3 * fb);
+  a.M = c->g.M;
+  a.st = c->d_st;
+  a.part = part_fwd(c);
+  a.pstride = (int)ncta_max(c);
+  a.cnt = cnt_fwd(c);
+  // enough CTAs per load to cover the SMs several times over, within the partial-sum slots
+  const int nblk = std::max(1, std::min(a.pstride, std::max(64, (152 * 8) / n)));
+  CK(launch_bicg<Tf>(BI_RESTART, a, n, nblk, c->stream));
+  bool any = true;
+  while (any) {
+    for (int k = 0; k < c->opt.check_every; ++k) {
+      CKS(apply_A<Tf>(c, n, a.p, a.v, &act));
+      CK(launch_bicg<Tf>(BI_ALPHA, a, n, nblk, c->stream));
+      CK(launch_bicg<Tf>(BI_S, a, n, nblk, c->stream));
+      CKS(apply_A<Tf>(c, n, a.s, a.t, &act));
+      CK(launch_bicg<Tf>(BI_OMEGA, a, n, nblk, c->stream));
+      CK(launch_bicg<Tf>(BI_X, a, n, nblk, c->stream));
+      CK(launch_bicg<Tf>(BI_P, a, n, nblk, c->stream));
+    }
+    CKS(read_states(c, n, st));
+    any = false;
+    for (int i = 0; i < n; ++i) {
+      act[i] = st[i].active;
+      any = any || act[i];
+    }
+  }
+  return HOM_OK;
+}
+
 // Solves A x = b (Eq. cg_form) for n loads; b = -Gamma0 * (C : E) for Kelvin loads dE (order 0,
 // device [n][6]) or b = b64 (higher orders).  The solution x64 is FP64 in both precisions.
 //  FP64 mode (Tf = double): Basic Scheme or CG in FP64 directly on x64.
@@ -461,6 +529,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   Tf* p = reinterpret_cast<Tf*>(vp);
   Tf* d = mixed ? reinterpret_cast<Tf*>(vd) : reinterpret_cast<Tf*>(x64);
   const bool basic = (c->opt.scheme == HOM_BASIC);
+  const bool bicg = (c->opt.scheme == HOM_BICGSTAB);
   // an FP32 sweep is asked for a reduction FP32 can deliver relative to its starting residual
   // The first sweep starts from b and aims at the tolerance itself where FP32 can reach it
   // (relative residuals down to kFirstSweepFloor); later sweeps ask for kSweepGain relative to
@@ -580,6 +649,10 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
     while (true) {
       bool any = false;
       for (int i = 0; i < n; ++i) any = any || act[i];
+      if (bicg && any) {
+        CKS(bicgstab_sweep<Tf>(c, n, d, r, p, st, act));
+        any = false;
+      }
       while (any) {
         for (int k = 0; k < c->opt.check_every; ++k) {
           auto fa = fwd_args<Tf, Tf>(c, FWD_CG, 6, 6);
@@ -1071,7 +1144,10 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if (c->opt.max_refine < 0) c->opt.max_refine = 0;
   if (c->opt.l2_budget_bytes <= 0) c->opt.l2_budget_bytes = 128LL << 20;
   if (c->opt.precision != HOM_FP64 && c->opt.precision != HOM_FP32_REFINE) { delete c; return HOM_ERR_ARG; }
-  if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG) { delete c; return HOM_ERR_ARG; }
+  if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG && c->opt.scheme != HOM_BICGSTAB) {
+    delete c;
+    return HOM_ERR_ARG;
+  }
   c->fp32 = (c->opt.precision == HOM_FP32_REFINE);
   c->nphase = n_phase;
   c->lam0 = lambda0;

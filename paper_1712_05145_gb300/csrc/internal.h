@@ -44,6 +44,11 @@ struct RhsState {
   int restart;       // 1: next CG step starts from p = r
   int status;        // 0 ok, 1 not converged, 2 numeric
   int best_iter;     // iteration at which `best` was last halved
+  // BiCGSTAB (L2 inner products): rho = <r_hat, r>, alpha, omega, beta; rr = <r, r>
+  double omega;
+  double rr;
+  int sconv;         // 1: the half step s already met the tolerance (omega = 0, x += alpha p)
+  int pad_;
 };
 
 // FWD_TAU: tau = (C - C0) : (in + E)     (polarization, Eq. auxiliary_problem)
@@ -125,6 +130,20 @@ struct InvArgs {
   const cx<T>* tw_n1;
   const cx<T>* tw_n2;
 };
+
+// BiCGSTAB vector updates with their FP64 reductions (one kernel per step kind, see bicgstab.cu)
+enum BicgStep { BI_RESTART = 0, BI_ALPHA = 1, BI_S = 2, BI_OMEGA = 3, BI_X = 4, BI_P = 5 };
+template <typename Tf>
+struct BicgArgs {
+  Tf *x, *r, *rh, *p, *v, *s, *t;  // [rhs][6][M] each
+  long long M;
+  RhsState* st;                    // [rhs]
+  double* part;                    // [rhs][2][pstride] partial sums
+  int pstride;
+  unsigned* cnt;                   // [rhs] tickets
+};
+template <typename Tf>
+cudaError_t launch_bicg(int step, const BicgArgs<Tf>& a, int nrhs, int nblk, cudaStream_t s);
 
 template <typename Tf, typename T>
 cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s);

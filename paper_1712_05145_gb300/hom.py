@@ -29,6 +29,7 @@ HOM_FP64 = 0
 HOM_FP32_REFINE = 1
 HOM_BASIC = 0
 HOM_CG = 1
+HOM_BICGSTAB = 2
 HOM_FIELD_STRAIN = 0
 HOM_FIELD_DISPLACEMENT = 1
 HOM_FIELD_STRESS = 2

@@ -328,6 +328,33 @@ def coated_sphere(n=32, r1=0.25, r2=0.4, e_core=100.0, e_coat=1000.0, e_matrix=4
     return Microstructure(phase, lame, lam0, mu0, "coated_sphere", {"r1": r1, "r2": r2})
 
 
+def plane_stress_lame(lam, mu):
+    """(lambda*, mu) such that the three-dimensional isotropic law with lambda*, applied to
+    in-plane strains (eps33 = eps13 = eps23 = 0), gives the in-plane stresses of the plane-stress
+    law of (lambda, mu): lambda* = 2 lambda mu / (lambda + 2 mu)."""
+    return 2.0 * lam * mu / (lam + 2.0 * mu), mu
+
+
+def hashin_2d(n=128, r1=0.25, r2=0.4, e_core=100.0, e_coat=1000.0, e_matrix=453.685, nu=0.3,
+              plane_stress=True):
+    """Hashin's structure of Sec. 4 on an n x n grid (N3 = 1): a centred disk core r < r1
+    (phase 0), a coating r1 <= r < r2 (phase 1) and the matrix outside (phase 2), with Young's
+    moduli e_core, e_coat, e_matrix and a common Poisson ratio nu.  plane_stress=True stores
+    plane-stress Lame parameters, else plane strain."""
+    y1, y2, _ = voxel_centres((n, n, 1))
+    d2 = y2[:, None] ** 2 + y1[None, :] ** 2
+    phase = np.full((1, n, n), 2, dtype=np.uint8)
+    phase[0][d2 < r2 * r2] = 1
+    phase[0][d2 < r1 * r1] = 0
+    lame = np.array([lame_from_young(e, nu) for e in (e_core, e_coat, e_matrix)])
+    if plane_stress:
+        lame = np.array([plane_stress_lame(l, m) for l, m in lame])
+    lam0, mu0 = midpoint_reference(lame)
+    return Microstructure(phase, lame, lam0, mu0, "hashin_2d",
+                          {"r1": r1, "r2": r2, "E": (e_core, e_coat, e_matrix), "nu": nu,
+                           "plane_stress": plane_stress})
+
+
 def random_field_strain(grid, n_fields, seed, dtype=np.float64):
     """Seeded uniform(-1, 1) Mandel strain fields, shape (n_fields, 6, N3, N2, N1)."""
     n1, n2, n3 = grid

@@ -18,7 +18,7 @@ def oracle_order0(ms, tol=1e-12):
     return [tensor_to_mandel(s) for s in sols], c_eff
 
 
-@pytest.mark.parametrize("precision,scheme", [(0, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("precision,scheme", [(0, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
 def test_order0_sphere16_fields_and_ceff(precision, scheme):
     from paper_1712_05145_gb300 import hom
     ms = synthetic.centred_sphere(16)
@@ -56,7 +56,7 @@ def test_config_c1_sphere32_basic_scheme_fp64():
     H.close()
 
 
-@pytest.mark.parametrize("precision,scheme", [(0, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("precision,scheme", [(0, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
 def test_config_c1_laminate32_closed_form(precision, scheme):
     from paper_1712_05145_gb300 import hom
     ms = synthetic.laminate((32, 32, 32))
@@ -122,4 +122,23 @@ def test_not_converged_is_reported():
     info = H.solve(0, 1e-12)
     assert all(i["status"] == hom.HOM_ERR_NOT_CONVERGED for i in info)
     assert all(i["iterations"] <= 3 for i in info)
+    H.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bicgstab_high_contrast_three_phases(precision):
+    """BiCGSTAB (the paper's Krylov solver) reaches the oracle's discrete solution on a
+    three-phase cell with a soft and a stiff phase (contrast 100 each way)."""
+    from paper_1712_05145_gb300 import hom
+    g = (16, 12, 8)
+    ms = synthetic.Microstructure(random_phase(g, 3, 41, p=[0.5, 0.3, 0.2]),
+                                  np.array([[1.0, 1.0], [1e2, 1e2], [1e-2, 1e-2]]), 50.0, 50.0)
+    ref_f, ref_c = oracle_order0(ms)
+    H = hom.Homogenization(ms, precision=precision, scheme=hom.HOM_BICGSTAB, max_iter=5000)
+    tol = 1e-11 if precision == 0 else 1e-8
+    info = H.solve(0, tol)
+    assert all(i["status"] == 0 for i in info), info
+    assert rel_err(H.effective(0), ref_c) < (1e-8 if precision == 0 else 1e-5)
+    for a in (0, 5):
+        assert rel_err(H.field(0, a), ref_f[a]) < (1e-8 if precision == 0 else 1e-4), a
     H.close()
