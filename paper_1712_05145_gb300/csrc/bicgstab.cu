@@ -62,7 +62,7 @@ __device__ __forceinline__ void bicg_finalize(int step, RhsState& s, const doubl
       else if (s.res < s.tol) s.active = 0;
       else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }
       else if (s.res < 0.5 * s.best) { s.best = s.res; s.best_iter = s.iter; }
-      else if (s.iter - s.best_iter >= (s.res < kNearFloor ? kStallItersNearFloor : kStallIters))
+      else if (s.stall && s.iter - s.best_iter >= (s.res < kNearFloor ? kStallItersNearFloor : kStallIters))
         s.active = 0;  // stalled: hand over to the FP64 residual sweep
       break;
     }

@@ -551,6 +551,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
     s.restart = 1;
     s.best = 1e300;
     s.best_iter = 0;
+    s.stall = mixed ? 1 : 0;   // FP64 CG runs to the tolerance: a restart there only loses information
     st[i] = s;
   }
   CKS(write_states(c, st));

@@ -48,7 +48,7 @@ struct RhsState {
   double omega;
   double rr;
   int sconv;         // 1: the half step s already met the tolerance (omega = 0, x += alpha p)
-  int pad_;
+  int stall;         // 1: end the sweep when the residual stalls (FP32 sweeps of the refinement)
 };
 
 // FWD_TAU: tau = (C - C0) : (in + E)     (polarization, Eq. auxiliary_problem)
@@ -164,6 +164,9 @@ size_t plane_smem_bytes(const Geo& g, size_t elem);
 size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2);
 // fills fd_h, fd_n2 and thr_plane of a geometry whose n1, n2, n3 are set
 void geo_finish(Geo& g);
+// resident CTAs per SM of the z pass for a launch shape (occupancy query, cached)
+template <typename T>
+int zpass_ctas_per_sm(int threads, size_t smem);
 // z-pass tiling for ncomp input components: fills tc_log2, ntiles, nthr
 template <typename T>
 void zpass_tiling(ZArgs<T>& a);

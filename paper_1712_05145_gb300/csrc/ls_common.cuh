@@ -22,9 +22,10 @@ constexpr int kEPT = 16;
 // elements per thread whose global loads a plane kernel issues together in its prologue and
 // epilogue loops
 constexpr int kBatch = 4;
-// A CG sweep whose residual has not halved for kStallIters iterations ends (the FP64
-// residual sweep then restarts it, or reports non-convergence).  Below kNearFloor (relative
-// residual) an FP32 sweep is close to its rounding floor and a shorter window applies.
+// An FP32 Krylov sweep (state flag `stall`) whose residual has not halved for kStallIters
+// iterations ends (the FP64 residual sweep then restarts it, or reports non-convergence).
+// Below kNearFloor (relative residual) an FP32 sweep is close to its rounding floor and a
+// shorter window applies.  FP64 sweeps run to the tolerance or the iteration cap.
 constexpr int kStallIters = 100;
 constexpr int kStallItersNearFloor = 25;
 constexpr double kNearFloor = 1e-5;
@@ -111,7 +112,7 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
       else if (s.res < s.tol) s.active = 0;
       else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }
       else if (s.res < 0.5 * s.best) { s.best = s.res; s.best_iter = s.iter; }
-      else if (s.iter - s.best_iter >= (s.res < kNearFloor ? kStallItersNearFloor : kStallIters))
+      else if (s.stall && s.iter - s.best_iter >= (s.res < kNearFloor ? kStallItersNearFloor : kStallIters))
         s.active = 0;  // sweep stalled: hand over to the FP64 residual sweep
       break;
     }

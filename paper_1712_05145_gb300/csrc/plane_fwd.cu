@@ -243,15 +243,37 @@ size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2) {
   return ((size_t)ncomp * cstride + g.n3) * elem;
 }
 
-// Widest power-of-two tile (<= 16 columns) whose pencils fit kEPT elements per thread
-// at <= 512 threads and <= 64 KB of shared memory.
+// z-pass tile: 2^lg consecutive spectrum columns (lg <= 4) whose pencils fit kEPT elements per
+// thread at <= 512 threads and <= 64 KB of shared memory.  Among the tiles whose row reads cover
+// at least one 32-byte sector, the one with the most resident warps per SM wins (ties: the
+// wider tile); at 128^3 in FP32 that is 4 columns (192 threads, 5 CTAs per SM) rather than 8
+// (384 threads, 2 CTAs per SM at the kernel's register count).
+static int zpass_threads(int ncomp, int n3, int lg) {
+  const long long e = (long long)ncomp * n3 * (1LL << lg);
+  int thr = (int)((e + kEPT - 1) / kEPT);
+  thr = ((thr + 31) / 32) * 32;
+  return thr < 128 ? 128 : thr;
+}
+
 template <typename T>
 void zpass_tiling(ZArgs<T>& a) {
   const size_t elem = sizeof(cx<T>);
-  int lg = 4;
-  while (lg > 0 && ((size_t)a.ncomp_in * a.g.n3 * ((size_t)1 << lg) > (size_t)kEPT * 512 ||
-                    zpass_smem_bytes(a.g, elem, a.ncomp_in, lg) > 64 * 1024))
-    --lg;
+  int best_lg = -1;
+  long long best_warps = -1;
+  for (int lg = 4; lg >= 0; --lg) {
+    const bool fits = (size_t)a.ncomp_in * a.g.n3 * ((size_t)1 << lg) <= (size_t)kEPT * 512 &&
+                      zpass_smem_bytes(a.g, elem, a.ncomp_in, lg) <= 64 * 1024;
+    if (!fits) continue;
+    if (best_lg >= 0 && ((size_t)1 << lg) * elem < 32) break;   // narrower than a sector
+    const int thr = zpass_threads(a.ncomp_in, a.g.n3, lg);
+    const long long warps =
+        (long long)zpass_ctas_per_sm<T>(thr, zpass_smem_bytes(a.g, elem, a.ncomp_in, lg)) * (thr / 32);
+    if (best_lg < 0 || warps > best_warps) {
+      best_lg = lg;
+      best_warps = warps;
+    }
+  }
+  const int lg = best_lg < 0 ? 0 : best_lg;
   a.tc_log2 = lg;
   const long long tc = 1LL << lg;
   a.ntiles = (int)((a.g.plane_c + tc - 1) / tc);
@@ -261,11 +283,7 @@ void zpass_tiling(ZArgs<T>& a) {
   a.fd_in = make_fastdiv((unsigned)(a.ncomp_in * tc));
   a.fd_out = make_fastdiv((unsigned)(a.ncomp_out * tc));
   a.fd_comp = make_fastdiv((unsigned)(a.g.n3 * tc));
-  const long long e = (long long)a.ncomp_in * a.g.n3 * tc;
-  int thr = (int)((e + kEPT - 1) / kEPT);
-  thr = ((thr + 31) / 32) * 32;
-  if (thr < 128) thr = 128;
-  a.nthr = thr;
+  a.nthr = zpass_threads(a.ncomp_in, a.g.n3, lg);
 }
 template void zpass_tiling<float>(ZArgs<float>&);
 template void zpass_tiling<double>(ZArgs<double>&);

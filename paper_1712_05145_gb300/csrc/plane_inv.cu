@@ -54,17 +54,18 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
     atomicAdd(a.prof + 1, (unsigned long long)psz);
   }
   const int nmain = n2 * h;
-  // the spectrum plane is contiguous (row pitch h): flat index e = row * h + col, loads of
-  // kBatch elements per thread in flight together
-  for (int e0 = tid; e0 < nmain; e0 += kBatch * nthr) {
-    cx<T> v[kBatch];
+  // the spectrum plane is contiguous (row pitch h): flat index e = row * h + col; kSBatch
+  // loads of a thread are in flight together
+  constexpr int kSBatch = 8;
+  for (int e0 = tid; e0 < nmain; e0 += kSBatch * nthr) {
+    cx<T> v[kSBatch];
     #pragma unroll
-    for (int j = 0; j < kBatch; ++j) {
+    for (int j = 0; j < kSBatch; ++j) {
       const int e = e0 + j * nthr;
       if (e < nmain) v[j] = Sp[e];
     }
     #pragma unroll
-    for (int j = 0; j < kBatch; ++j) {
+    for (int j = 0; j < kSBatch; ++j) {
       const int e = e0 + j * nthr;
       if (e < nmain) {
         const int row = (int)g.fd_h.div((unsigned)e), col = e - row * h;

@@ -1,4 +1,7 @@
 // z-pencil pass of the Lippmann-Schwinger step: z FFTs and the Green contraction.
+#include <map>
+#include <utility>
+
 #include "ls_common.cuh"
 
 namespace hom {
@@ -85,11 +88,32 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
   }
 
   const int per_c = n3 * TC;
-  for (int e = tid; e < a.ncomp_in * per_c; e += nthr) {
-    const int c = (int)a.fd_comp.div((unsigned)e), ec = e - c * per_c;
-    const int tc = ec & (TC - 1), n = ec >> tc_log2;
-    const long long f = f0 + tc;
-    buf[c * cstride + ec] = (f < g.plane_c) ? Sr[(long long)(c * n3 + n) * g.plane_c + f] : mk<T>(0, 0);
+  {
+    // kZBatch loads per thread in flight together, then the shared-memory stores
+    constexpr int kZBatch = 8;
+    const int total = a.ncomp_in * per_c;
+    for (int e0 = tid; e0 < total; e0 += kZBatch * nthr) {
+      cx<T> v[kZBatch];
+      #pragma unroll
+      for (int j = 0; j < kZBatch; ++j) {
+        const int e = e0 + j * nthr;
+        v[j] = mk<T>(0, 0);
+        if (e < total) {
+          const int c = (int)a.fd_comp.div((unsigned)e), ec = e - c * per_c;
+          const int tc = ec & (TC - 1), n = ec >> tc_log2;
+          const long long f = f0 + tc;
+          if (f < g.plane_c) v[j] = Sr[(long long)(c * n3 + n) * g.plane_c + f];
+        }
+      }
+      #pragma unroll
+      for (int j = 0; j < kZBatch; ++j) {
+        const int e = e0 + j * nthr;
+        if (e < total) {
+          const int c = (int)a.fd_comp.div((unsigned)e);
+          buf[c * cstride + e - c * per_c] = v[j];
+        }
+      }
+    }
   }
   __syncthreads();
   const ZAddr za{tc_log2, cstride, TC};
@@ -171,6 +195,27 @@ cudaError_t launch_zpass(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
   k<<<grid, a.nthr, smem, s>>>(a);
   return cudaGetLastError();
 }
+
+// resident CTAs per SM of the z pass at `threads` threads and `smem` bytes (0 if it cannot run);
+// cached per host thread, since the answer depends only on the arguments
+template <typename T>
+int zpass_ctas_per_sm(int threads, size_t smem) {
+  thread_local std::map<std::pair<int, size_t>, int> cache;
+  const auto key = std::make_pair(threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  auto k = zpass_kernel<T, kEPT>;
+  int nb = 0;
+  if (set_smem(k, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 0;
+  }
+  cache[key] = nb;
+  return nb;
+}
+template int zpass_ctas_per_sm<float>(int, size_t);
+template int zpass_ctas_per_sm<double>(int, size_t);
 
 template cudaError_t launch_zpass<float>(const ZArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_zpass<double>(const ZArgs<double>&, int, cudaStream_t);
