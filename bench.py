@@ -99,13 +99,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def kernel_source_digest():
+# source files each profiled kernel kind is compiled from (its translation unit and the headers
+# it includes); the committed DRAM counters of a kind are used only while these are unchanged
+KERNEL_SOURCES = {
+    "plane_fwd": ["plane_fwd.cu"], "plane_fwd_f64": ["plane_fwd.cu"],
+    "zpass": ["zpass.cu"], "zpass_f64": ["zpass.cu"],
+    "plane_inv": ["plane_inv.cu"], "plane_inv_f64": ["plane_inv.cu"],
+    "ypass": ["ypass.cu"], "ypass_f64": ["ypass.cu"],
+}
+KERNEL_HEADERS = ["ls_common.cuh", "common.cuh", "internal.h"]
+
+
+def kernel_source_digest(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1712_05145_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in KERNEL_SOURCES.get(kernel, []) + KERNEL_HEADERS:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -116,10 +126,10 @@ def ncu_traffic(kernel):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_digest") != kernel_source_digest():
-        return None
     ent = d.get("kernels", {}).get(kernel)
-    return None if ent is None else ent.get("dram_bytes_per_launch_full")
+    if ent is None or ent.get("source_digest") != kernel_source_digest(kernel):
+        return None
+    return ent.get("dram_bytes_per_launch_full")
 
 
 def cpu_baseline():

@@ -19,10 +19,12 @@
  *  - Symmetric tensors are Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12);
  *    vectors are 3 components (x1, x2, x3).  6x6 and 6xK matrices are row-major.
  *  - Orders are counted from 0: order 0 is the classical cell problem (the paper's
- *    alpha = 1), order 1 and 2 are the paper's alpha = 2 and alpha = 3.
+ *    alpha = 1), order o >= 1 is the paper's alpha = o + 1 (orders up to 4).
  *  - Unit loads: order 0, load A = 0..5 is the Mandel unit strain E^A; order 1,
  *    load 3*A + k is E(Y) = E^A Y_k (18 loads); order 2, load 6*A + P is
- *    E(Y) = E^A Y_k Y_l / (1 + delta_kl) with (k, l) the P-th Mandel pair (36 loads).
+ *    E(Y) = E^A Y_k Y_l / (1 + delta_kl) with (k, l) the P-th Mandel pair (36 loads);
+ *    order o >= 3, E(Y) = E^A Y^K / K! for the multisets K of o directions in
+ *    lexicographic order (60 loads for o = 3, 90 for o = 4).
  *  - Spectral operators use the discrete wave vector xi_i = 2 pi k_i / (N_i h) with the
  *    Nyquist component (k_i = N_i/2 on even axes) taken as 0.
  *  - Errors are returned as hom_status; no C++ exception crosses the ABI.  After an
@@ -111,7 +113,8 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
                               const double* lame, double lambda0, double mu0,
                               const hom_options* opt, hom_t* out);
 
-/* Solves problem `order` (0, 1 or 2) for its loads to relative residual tol:
+/* Solves problem `order` (0 to 4: the paper's alpha = order + 1) for its loads to relative
+ * residual tol:
  * ||b - A eps||_L2 / ||b||_L2 < tol with A = Id + Gamma0 * (C - C0) (Eq. cg_form); for the
  * Basic Scheme this is the paper's Cauchy quantity ||eps_{n+1} - eps_n|| / ||eps_0||.
  *  order 0: n_loads macroscopic strains, loads = double [n_loads][6] Mandel host array, or
@@ -120,7 +123,11 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
  *           component, k the direction), or loads = double [n_loads][18] host array of
  *           coefficients of those unit loads (n_loads <= 64), each solved as one system.
  *           Every unit load used needs the unit strain e_A among the converged order-0 loads.
- *  order 2: requires order 1 solved for its 18 unit loads; loads must be NULL (36 loads).
+ *  order o >= 2: requires order o - 1 solved for its unit loads; loads must be NULL.  The unit
+ *           loads are E(Y) = E^A Y^K / K! for the multisets K of o directions: 6 x (o+1)(o+2)/2
+ *           loads (36, 60, 90 for o = 2, 3, 4), load A * nK + (index of K), K ordered as the
+ *           Mandel pairs (11, 22, 33, 23, 13, 12) for o = 2 and lexicographically (sorted
+ *           tuples, 111 < 112 < ... < 333) for o >= 3.
  *  info     host array of one hom_solve_info per load (nullable); caller-owned.
  * The correctors stay on the device, owned by the handle, until hom_destroy or the next
  * solve of the same order.  Returns HOM_ERR_NOT_CONVERGED if any load missed tol. */
@@ -131,14 +138,14 @@ HOM_API hom_status hom_solve(hom_t h, int32_t order, int32_t n_loads, const doub
  *  order 0: 6 x n_loads, column A = <C : (E^A + eps^A)> (the 6x6 C_eff for unit loads);
  *  order 1: 6 x n_loads (18 for the unit loads), column = <C : eps_2 + p_2> (mean order-2
  *           stress of the paper's alpha = 2);
- *  order 2: 6 x 36, column = <C : eps_3 + p_3>. */
+ *  order o >= 2: 6 x (its loads), column = <C : eps_{o+1} + p_{o+1}>. */
 HOM_API hom_status hom_effective(hom_t h, int32_t order, double* out);
 
 /* Copies one corrector field of a solved order to dst (double):
  *  HOM_FIELD_STRAIN       6 x [N3][N2][N1] Mandel strain fluctuation eps;
  *  HOM_FIELD_DISPLACEMENT 3 x [N3][N2][N1] zero-mean displacement u with e_y(u) = eps;
  *  HOM_FIELD_STRESS       6 x [N3][N2][N1] Mandel stress (C : (E + eps) for order 0,
- *                         C : eps + p for orders 1 and 2).
+ *                         C : eps + p for orders >= 1).
  * dst is a device pointer if dst_on_device != 0, else a host pointer. */
 HOM_API hom_status hom_get_field(hom_t h, int32_t order, int32_t load, int32_t kind, double* dst,
                                  int32_t dst_on_device);

@@ -172,7 +172,7 @@ class Hierarchy:
     def order3(self):
         """alpha = 3 for the 36 loads E^A Y_k Y_l / (1 + d_kl); returns D_2 (6 x 36 Mandel)."""
         pb = self.pb
-        self.eps3 = {}
+        self.eps3, self.u3, self.s3 = {}, {}, {}
         cols = []
         for a in range(6):
             for pair in range(6):
@@ -180,6 +180,110 @@ class Hierarchy:
                 eps = self._solve(rhs_order_alpha(pb, p, g))
                 self.eps3[(a, pair)] = eps
                 s = pb.stress(eps) + p
+                self.u3[(a, pair)] = displacement_from_strain(eps, pb.grid)
+                self.s3[(a, pair)] = s
                 cols.append(tensor_to_mandel(s.reshape(3, 3, -1).mean(axis=-1)))
         self.d2 = np.stack(cols, axis=1)
         return self.d2
+
+
+# --- any order alpha >= 2, from the Definition with exact monomial loads -------------------
+#
+# A unit load of order alpha is E(Y) = E^A m_K(Y) with K a multiset of alpha - 1 directions and
+# the monomial m_K = Y^K / K! (so that the derivative d^K m_K = 1).  With the separation ansatz
+# u_beta(Y, y) = sum_J X_beta^(A,J)(y) d^J m(Y) (J over multisets of beta - 1 directions), the
+# polarization and body force of the Definition,
+#     p_alpha = C : e_Y(u_{alpha-1}),   g_alpha = div_Y [C : e_y(u_{alpha-1}) + p_{alpha-1}],
+# become sums over the order-(alpha-1) correctors with the coefficients d_j d^J m_K, which are
+# numbers because m_K has degree alpha - 1.  The coefficients are computed by differentiating
+# the monomial, not from a table of which J and j pair up.
+
+def multisets(size):
+    """Multisets of `size` directions from {0, 1, 2} as sorted tuples, in lexicographic order
+    (the unit-load order of alpha = size + 1 >= 4)."""
+    out = []
+
+    def rec(prefix, start):
+        if len(prefix) == size:
+            out.append(tuple(prefix))
+            return
+        for d in range(start, 3):
+            rec(prefix + [d], d)
+
+    rec([], 0)
+    return out
+
+
+def monomial(K):
+    """m_K = Y^K / K! as (exponents, coefficient)."""
+    e = [K.count(d) for d in range(3)]
+    c = 1.0
+    for n in e:
+        for i in range(2, n + 1):
+            c /= i
+    return e, c
+
+
+def derivative_value(mono, dirs):
+    """d^dirs m as a number, for a monomial whose degree equals len(dirs) (else None if the
+    result still depends on Y, 0.0 if it vanishes)."""
+    e, c = list(mono[0]), mono[1]
+    for d in dirs:
+        if e[d] == 0:
+            return 0.0
+        c *= e[d]
+        e[d] -= 1
+    return c if sum(e) == 0 else None
+
+
+def load_key(alpha, K):
+    """Dictionary key of the unit load (A fixed) of order alpha for the sorted multiset K."""
+    if alpha == 1:
+        return ()
+    return tuple(sorted(K))
+
+
+class GeneralHierarchy:
+    """Orders alpha >= 2 for all unit loads from the order-1 correctors of a ``Hierarchy``
+    (paper numbering; the C-ABI's order is alpha - 1)."""
+
+    def __init__(self, base):
+        self.base = base
+        pb = base.pb
+        # order-1 displacement correctors and stresses, keyed by (A, ())
+        self.U = {1: {(a, ()): base.chi[a] for a in range(6)}}
+        self.S = {1: {(a, ()): base.sig1[a] for a in range(6)}}
+        self.eps, self.D = {}, {}
+        self.pb = pb
+
+    def loads(self, alpha):
+        return multisets(alpha - 1)
+
+    def solve(self, alpha):
+        """Solves order alpha (needs alpha - 1); returns D[alpha] (6 x 6 * n_K Mandel), columns
+        ordered A-major over ``loads(alpha)``."""
+        pb = self.pb
+        U, S = self.U[alpha - 1], self.S[alpha - 1]
+        Js = multisets(alpha - 2)
+        self.U[alpha], self.S[alpha], self.eps[alpha] = {}, {}, {}
+        cols = []
+        for a in range(6):
+            for K in self.loads(alpha):
+                m = monomial(K)
+                p = np.zeros((3, 3) + pb.phase.shape)
+                g = np.zeros((3,) + pb.phase.shape)
+                for J in Js:
+                    for j in range(3):
+                        c = derivative_value(m, list(J) + [j])
+                        if not c:
+                            continue
+                        p += c * pb.stress(sym_outer_vec_dir(U[(a, J)], j))
+                        g += c * S[(a, J)][:, j]
+                eps = self.base._solve(rhs_order_alpha(pb, p, g))
+                s = pb.stress(eps) + p
+                self.eps[alpha][(a, K)] = eps
+                self.U[alpha][(a, K)] = displacement_from_strain(eps, pb.grid)
+                self.S[alpha][(a, K)] = s
+                cols.append(tensor_to_mandel(s.reshape(3, 3, -1).mean(axis=-1)))
+        self.D[alpha] = np.stack(cols, axis=1)
+        return self.D[alpha]

@@ -14,14 +14,27 @@ namespace hom {
 //          g_i = w [s^(A,k)_il + s^(A,l)_ik],  s = C : eps_2 + p_2  from the order-1 correctors.
 //  For order 1, map selects the loads: load L is the unit load u = map.unit[L] = 3A+k, and the
 //  order-0 correctors of E^A are those of order-0 load map.a0[A].
+//  For orders o >= 2 (the paper's alpha = o + 1) the unit loads are E^A m_K(Y), K a multiset
+//  of o directions and m_K = Y^K / K!, load L = A * nK + (index of K); then
+//      p = C : sum_j sym(u^(A, K - e_j) (x) e_j),   g = sum_j s^(A, K - e_j) e_j,
+//  over the distinct directions j of K, with u and s = C : eps + p the displacement and stress
+//  correctors of order o - 1 (table rec).
 struct UnitMap {
   int unit[18];
   int a0[6];
 };
+constexpr int kMaxOrder = 4;     // orders 0..4 (the paper's alpha = 1..5)
+constexpr int kMaxMultisets = 15;
+struct RecTable {
+  int nK, nKprev;                  // multisets of this order and of the previous one
+  int nterm[kMaxMultisets];
+  int dir[kMaxMultisets][3];
+  int src[kMaxMultisets][3];       // position of K - e_dir among the previous order's multisets
+};
 template <typename Tf>
-cudaError_t launch_rhs_pointwise(int order, int nload, const UnitMap& map, const Tf* disp, const Tf* eps,
-                                 const Tf* pprev, const double* EK, const uint8_t* phase, const double* mat,
-                                 long long M, Tf* out9, Tf* pf, cudaStream_t s);
+cudaError_t launch_rhs_pointwise(int order, int nload, const UnitMap& map, const RecTable& rec, const Tf* disp,
+                                 const Tf* eps, const Tf* pprev, const double* EK, const uint8_t* phase,
+                                 const double* mat, long long M, Tf* out9, Tf* pf, cudaStream_t s);
 
 // out[l][i] = sum_u W[l][u] in[u][i] for l < nout, u < nin, i < per (linear combinations of loads).
 cudaError_t launch_combine_loads(const double* in, int nin, const double* W, int nout, long long per, double* out,

@@ -43,7 +43,8 @@ __device__ __forceinline__ void add_sym_vec_dir(double* t, const double* v, int 
 }
 
 template <typename Tf>
-__global__ void rhs_pointwise_kernel(int order, int nload, const UnitMap map, const Tf* __restrict__ disp,
+__global__ void rhs_pointwise_kernel(int order, int nload, const UnitMap map, const RecTable rec,
+                                     const Tf* __restrict__ disp,
                                      const Tf* __restrict__ eps,
                                      const Tf* __restrict__ pprev, const double* __restrict__ EK,
                                      const uint8_t* __restrict__ phase, const double* __restrict__ mat, long long M,
@@ -66,27 +67,19 @@ __global__ void rhs_pointwise_kernel(int order, int nload, const UnitMap map, co
       k2t(sk, st);
       for (int i = 0; i < 3; ++i) g[i] = st[tidx(i, k)];
     } else {
-      const int A = L / 6, P = L - 6 * (L / 6);
-      const int pk[6] = {0, 1, 2, 1, 0, 0}, pl[6] = {0, 1, 2, 2, 2, 1};
-      const int k = pk[P], l = pl[P];
-      const double w = (k == l) ? 0.5 : 1.0;
-      const int Lk = 3 * A + k, Ll = 3 * A + l;
-      double uk[3], ul[3];
-      for (int i = 0; i < 3; ++i) {
-        uk[i] = (double)disp[((long long)Lk * 3 + i) * M + v];
-        ul[i] = (double)disp[((long long)Ll * 3 + i) * M + v];
+      const int A = L / rec.nK, K = L - A * rec.nK;
+      g[0] = g[1] = g[2] = 0.0;
+      for (int q = 0; q < rec.nterm[K]; ++q) {
+        const int d = rec.dir[K][q];
+        const long long Ls = (long long)A * rec.nKprev + rec.src[K][q];
+        double u[3], sq[6], tq[6];
+        for (int i = 0; i < 3; ++i) u[i] = (double)disp[(Ls * 3 + i) * M + v];
+        add_sym_vec_dir(t, u, d, 1.0);
+        for (int c = 0; c < 6; ++c)
+          sq[c] = (c == 0 ? ch : cd) * (double)eps[(Ls * 6 + c) * M + v] + (double)pprev[(Ls * 6 + c) * M + v];
+        k2t(sq, tq);
+        for (int i = 0; i < 3; ++i) g[i] += tq[tidx(i, d)];
       }
-      add_sym_vec_dir(t, uk, l, w);
-      add_sym_vec_dir(t, ul, k, w);
-      double sk[6], sl[6], tk[6], tl[6];
-      for (int c = 0; c < 6; ++c) {
-        const double cc = (c == 0 ? ch : cd);
-        sk[c] = cc * (double)eps[((long long)Lk * 6 + c) * M + v] + (double)pprev[((long long)Lk * 6 + c) * M + v];
-        sl[c] = cc * (double)eps[((long long)Ll * 6 + c) * M + v] + (double)pprev[((long long)Ll * 6 + c) * M + v];
-      }
-      k2t(sk, tk);
-      k2t(sl, tl);
-      for (int i = 0; i < 3; ++i) g[i] = w * (tk[tidx(i, l)] + tl[tidx(i, k)]);
     }
     double kk[6];
     t2k(t, kk);
@@ -130,12 +123,14 @@ static int blocks_for(long long n) {
 }
 
 template <typename Tf>
-cudaError_t launch_rhs_pointwise(int order, int nload, const UnitMap& map, const Tf* disp, const Tf* eps,
-                                 const Tf* pprev, const double* EK, const uint8_t* phase, const double* mat,
-                                 long long M, Tf* out9, Tf* pf, cudaStream_t s) {
+cudaError_t launch_rhs_pointwise(int order, int nload, const UnitMap& map, const RecTable& rec, const Tf* disp,
+                                 const Tf* eps, const Tf* pprev, const double* EK, const uint8_t* phase,
+                                 const double* mat, long long M, Tf* out9, Tf* pf, cudaStream_t s) {
+  if (order >= 2 && (rec.nK < 1 || rec.nK > kMaxMultisets || (long long)nload != 6LL * rec.nK))
+    return cudaErrorInvalidValue;
   count_launch();
-  rhs_pointwise_kernel<Tf><<<blocks_for((long long)nload * M), 256, 0, s>>>(order, nload, map, disp, eps, pprev,
-                                                                             EK, phase, mat, M, out9, pf);
+  rhs_pointwise_kernel<Tf><<<blocks_for((long long)nload * M), 256, 0, s>>>(order, nload, map, rec, disp, eps,
+                                                                             pprev, EK, phase, mat, M, out9, pf);
   return cudaGetLastError();
 }
 
@@ -167,12 +162,12 @@ cudaError_t launch_stress_field(const Tf* eps, const double* EK, const Tf* pf, c
   return cudaGetLastError();
 }
 
-template cudaError_t launch_rhs_pointwise<float>(int, int, const UnitMap&, const float*, const float*, const float*,
-                                                 const double*, const uint8_t*, const double*, long long, float*,
-                                                 float*, cudaStream_t);
-template cudaError_t launch_rhs_pointwise<double>(int, int, const UnitMap&, const double*, const double*,
-                                                  const double*, const double*, const uint8_t*, const double*,
-                                                  long long, double*, double*, cudaStream_t);
+template cudaError_t launch_rhs_pointwise<float>(int, int, const UnitMap&, const RecTable&, const float*,
+                                                 const float*, const float*, const double*, const uint8_t*,
+                                                 const double*, long long, float*, float*, cudaStream_t);
+template cudaError_t launch_rhs_pointwise<double>(int, int, const UnitMap&, const RecTable&, const double*,
+                                                  const double*, const double*, const double*, const uint8_t*,
+                                                  const double*, long long, double*, double*, cudaStream_t);
 template cudaError_t launch_stress_field<float>(const float*, const double*, const float*, const uint8_t*,
                                                 const double*, long long, double*, cudaStream_t);
 template cudaError_t launch_stress_field<double>(const double*, const double*, const double*, const uint8_t*,

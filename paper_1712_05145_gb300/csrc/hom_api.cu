@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -100,7 +101,7 @@ struct hom_ctx {
   void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t
   size_t bicg_bytes = 0;
   size_t work_bytes[4] = {0, 0, 0, 0};
-  OrderData ord[3];
+  OrderData ord[kMaxOrder + 1];
   size_t bytes = 0;
   std::vector<void*> allocs;
   std::string err;
@@ -812,11 +813,66 @@ hom_status displacements(hom_ctx* c, int order) {
 
 // Right-hand sides b = -Gamma0 * (p_alpha + theta_alpha) of order 1 or 2 (Sec. 3, modified
 // initialization), in FP64, with p_alpha kept in pf for the effective tensor.
+// Multisets K of `o` directions, in the load order of order o: o = 1: k; o = 2: the Mandel
+// pairs (11, 22, 33, 23, 13, 12); o >= 3: sorted tuples in lexicographic order.
+std::vector<std::vector<int>> order_multisets(int o) {
+  std::vector<std::vector<int>> out;
+  if (o == 1) return {{0}, {1}, {2}};
+  if (o == 2) return {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  std::vector<int> cur;
+  std::function<void(int)> rec = [&](int start) {
+    if ((int)cur.size() == o) {
+      out.push_back(cur);
+      return;
+    }
+    for (int d = start; d < 3; ++d) {
+      cur.push_back(d);
+      rec(d);
+      cur.pop_back();
+    }
+  };
+  rec(0);
+  return out;
+}
+
+int loads_of_order(int o) { return o == 0 ? 6 : 6 * (o + 1) * (o + 2) / 2; }
+
+// For every multiset K of order o >= 2: the distinct directions j of K and the position of
+// K - e_j among the multisets of order o - 1.
+RecTable rec_table(int o) {
+  RecTable t{};
+  const auto cur = order_multisets(o), prev = order_multisets(o - 1);
+  t.nK = (int)cur.size();
+  t.nKprev = (int)prev.size();
+  for (int k = 0; k < t.nK; ++k) {
+    int n = 0;
+    for (int j = 0; j < 3; ++j) {
+      auto it = std::find(cur[k].begin(), cur[k].end(), j);
+      if (it == cur[k].end()) continue;
+      std::vector<int> rest = cur[k];
+      rest.erase(rest.begin() + (it - cur[k].begin()));
+      std::sort(rest.begin(), rest.end());
+      int idx = -1;
+      for (int q = 0; q < t.nKprev && idx < 0; ++q) {
+        std::vector<int> pq = prev[q];
+        std::sort(pq.begin(), pq.end());
+        if (pq == rest) idx = q;
+      }
+      t.dir[k][n] = j;
+      t.src[k][n] = idx;
+      ++n;
+    }
+    t.nterm[k] = n;
+  }
+  return t;
+}
+
 // Right-hand sides of order `order` (b = -Gamma0 * (p + theta), Sec. 3) and the polarizations p:
 // order 1 for the nu unit loads map.unit[0..nu) (order-0 correctors through map.a0), order 2 for
 // the 36 unit loads.
 hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf, const UnitMap& map, int nu) {
-  const int n = (order == 1) ? nu : 36;
+  const int n = (order == 1) ? nu : loads_of_order(order);
+  const RecTable rec = (order >= 2) ? rec_table(order) : RecTable{};
   CKS(displacements(c, order - 1));
   const OrderData& lo = c->ord[order - 1];
   void* v9;
@@ -826,9 +882,9 @@ hom_status build_rhs(hom_ctx* c, int order, double* b, double* pf, const UnitMap
   if (order == 1)
     CK(cudaMemcpyAsync(c->d_E, c->ord[0].loadsK.data(), sizeof(double) * c->ord[0].loadsK.size(),
                        cudaMemcpyHostToDevice, c->stream));
-  CK(launch_rhs_pointwise<double>(order, n, map, reinterpret_cast<const double*>(lo.disp),
+  CK(launch_rhs_pointwise<double>(order, n, map, rec, reinterpret_cast<const double*>(lo.disp),
                                   reinterpret_cast<const double*>(lo.eps),
-                                  order == 2 ? reinterpret_cast<const double*>(lo.pf) : nullptr, c->d_E, c->d_phase,
+                                  order >= 2 ? reinterpret_cast<const double*>(lo.pf) : nullptr, c->d_E, c->d_phase,
                                   c->d_mat64, c->g.M, f9, pf, c->stream));
   int chunk;
   cx<double>* S = spec<double>(c, &chunk);
@@ -941,8 +997,8 @@ hom_status solve_higher(hom_ctx* c, int order, int n, const double* W, double to
       for (int l = 0; l < n; ++l)
         for (int j = 0; j < nu; ++j) Wu[(size_t)l * nu + j] = W[l * 18 + map.unit[j]];
     }
-  } else if (!c->ord[1].unit) {
-    return fail(c, HOM_ERR_ORDER, "order 2 needs order 1 solved for its 18 unit loads");
+  } else if (!c->ord[order - 1].unit) {
+    return fail(c, HOM_ERR_ORDER, "order %d needs order %d solved for its unit loads", order, order - 1);
   }
   CKS(alloc_order(c, order, n, true));
   OrderData& o = c->ord[order];
@@ -978,7 +1034,7 @@ hom_status solve_higher(hom_ctx* c, int order, int n, const double* W, double to
     if (dW) dfree(c, dW, sizeof(double) * Wu.size());
     if (st != HOM_OK) return st;
   } else {
-    CKS(build_rhs(c, order, b, reinterpret_cast<double*>(o.pf), map, order == 1 ? nu : 36));
+    CKS(build_rhs(c, order, b, reinterpret_cast<double*>(o.pf), map, order == 1 ? nu : n));
   }
   hom_status s = solve_system<Tf>(c, n, nullptr, b, reinterpret_cast<double*>(o.eps), tol, info);
   if (s != HOM_OK && s != HOM_ERR_NOT_CONVERGED) return s;
@@ -1049,7 +1105,7 @@ HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t
   if (!grid) return -1;
   const long long n1 = grid[0], n2 = grid[1], n3 = grid[2];
   if (n1 < 4 || (n1 & 1) || !fft_length_supported((int)(n1 / 2)) || !fft_length_supported((int)n2) ||
-      !z_length_supported((int)n3) || order < 0 || order > 2)
+      !z_length_supported((int)n3) || order < 0 || order > kMaxOrder)
     return -1;
   const bool fp32 = (precision == HOM_FP32_REFINE);
   const long long M = n1 * n2 * n3, plane_c = n2 * (n1 / 2 + 1);
@@ -1063,7 +1119,7 @@ HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t
   long long b = M + (1LL << 20);                 // phase, tables, states
   b += scratch(fp32 ? 8 : 16);
   if (fp32) b += scratch(16);
-  const long long nl = order >= 1 ? (order == 2 ? 36 : 18) : 6, tf = fp32 ? 4 : 8;
+  const long long nl = loads_of_order(order), tf = fp32 ? 4 : 8;
   b += 2 * nl * 6 * M * tf;                      // r, p
   long long slot3 = fp32 ? nl * 6 * M * 4 : 0;   // FP32 correction d
   if (order >= 1) {
@@ -1072,8 +1128,8 @@ HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t
   }
   b += slot3;
   b += 6 * 9 * M * 8;                            // order-0 strain and displacement
-  if (order >= 1) b += 18 * 15 * M * 8;          // order-1 strain, displacement, polarization
-  if (order >= 2) b += 36 * 15 * M * 8;
+  for (int o = 1; o <= order; ++o)               // strain, displacement, polarization of each order
+    b += (long long)loads_of_order(o) * 15 * M * 8;
   return (int64_t)((double)b * 1.05) + (16LL << 20);
 }
 
@@ -1257,28 +1313,27 @@ HOM_API hom_status hom_solve(hom_t c, int32_t order, int32_t n_loads, const doub
                              hom_solve_info* info) {
   if (!c) return HOM_ERR_ARG;
   if (!(tol > 0.0)) return fail(c, HOM_ERR_ARG, "tol must be > 0");
-  if (order < 0 || order > 2) return fail(c, HOM_ERR_ARG, "order must be 0, 1 or 2");
+  if (order < 0 || order > kMaxOrder) return fail(c, HOM_ERR_ARG, "order must be in 0..%d", kMaxOrder);
+  for (int k = order + 1; k <= kMaxOrder; ++k) c->ord[k].solved = false;
   if (order == 0) {
     int n = loads ? n_loads : 6;
     if (n < 1 || n > 64) return fail(c, HOM_ERR_ARG, "n_loads must be in 1..64");
-    for (int k = order + 1; k < 3; ++k) c->ord[k].solved = false;
     return c->fp32 ? solve_order0<float>(c, n, loads, tol, info) : solve_order0<double>(c, n, loads, tol, info);
   }
-  if (order == 2 && loads) return fail(c, HOM_ERR_ARG, "order 2 takes only its unit loads (loads = NULL)");
-  int n = (order == 1) ? 18 : 36;
+  if (order >= 2 && loads) return fail(c, HOM_ERR_ARG, "orders >= 2 take only their unit loads (loads = NULL)");
+  int n = loads_of_order(order);
   if (order == 1 && loads) {
     n = n_loads;
     if (n < 1 || n > 64) return fail(c, HOM_ERR_ARG, "n_loads must be in 1..64");
   }
   c->ord[order].solved = false;
-  if (order == 1) c->ord[2].solved = false;
   return c->fp32 ? solve_higher<float>(c, order, n, loads, tol, info)
                  : solve_higher<double>(c, order, n, loads, tol, info);
 }
 
 HOM_API hom_status hom_effective(hom_t c, int32_t order, double* out) {
   if (!c || !out) return HOM_ERR_ARG;
-  if (order < 0 || order > 2) return fail(c, HOM_ERR_ARG, "order must be 0, 1 or 2");
+  if (order < 0 || order > kMaxOrder) return fail(c, HOM_ERR_ARG, "order must be in 0..%d", kMaxOrder);
   const OrderData& o = c->ord[order];
   if (o.eff.empty()) return fail(c, HOM_ERR_ORDER, "order %d has not been solved", order);
   std::memcpy(out, o.eff.data(), sizeof(double) * o.eff.size());
@@ -1288,7 +1343,7 @@ HOM_API hom_status hom_effective(hom_t c, int32_t order, double* out) {
 HOM_API hom_status hom_get_field(hom_t c, int32_t order, int32_t load, int32_t kind, double* dst,
                                  int32_t dst_on_device) {
   if (!c || !dst) return HOM_ERR_ARG;
-  if (order < 0 || order > 2) return fail(c, HOM_ERR_ARG, "order must be 0, 1 or 2");
+  if (order < 0 || order > kMaxOrder) return fail(c, HOM_ERR_ARG, "order must be in 0..%d", kMaxOrder);
   const OrderData& o = c->ord[order];
   if (!o.eps || o.eff.empty()) return fail(c, HOM_ERR_ORDER, "order %d has not been solved", order);
   if (load < 0 || load >= o.nloads) return fail(c, HOM_ERR_ARG, "load out of range");

@@ -211,11 +211,16 @@ def hom_create(grid, phase, lame, lambda0, mu0, options=None):
     return h
 
 
+def loads_of_order(order):
+    """Unit loads of an order: 6 for order 0, 6 (o+1)(o+2)/2 for order o >= 1."""
+    return 6 if order == 0 else 6 * (order + 1) * (order + 2) // 2
+
+
 def hom_solve(h, order, tol, loads=None):
     """Returns a list of per-load info dicts; raises HomError on any failure except
     non-convergence, which is reported through each load's status."""
     lib = load_library()
-    nl = {0: 6, 1: 18, 2: 36}[order] if loads is None else int(np.asarray(loads).shape[0])
+    nl = loads_of_order(order) if loads is None else int(np.asarray(loads).shape[0])
     arr = None
     if loads is not None:
         arr = np.ascontiguousarray(loads, dtype=np.float64).reshape(nl, 6 if order == 0 else 18)

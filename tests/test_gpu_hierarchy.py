@@ -77,3 +77,49 @@ def test_order_dependencies_enforced():
     with pytest.raises(hom.HomError):
         H.solve(1, 1e-8)
     H.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_general(oracle_asym):
+    from oracle.hierarchy import GeneralHierarchy
+    ms, oh = oracle_asym
+    G = GeneralHierarchy(oh)
+    for alpha in (2, 3, 4, 5):
+        G.solve(alpha)
+    return ms, G
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_orders_3_and_4_match_oracle(oracle_general, precision):
+    """Orders 3 and 4 (the paper's alpha = 4, 5) from the recursive right-hand-side builder."""
+    from oracle.hierarchy import multisets
+    from paper_1712_05145_gb300 import hom
+    ms, G = oracle_general
+    H = hom.Homogenization(ms, precision=precision)
+    tol = 1e-12 if precision == 0 else 1e-9
+    for order in range(5):
+        info = H.solve(order, tol)
+        assert len(info) == hom.loads_of_order(order)
+        assert all(i["status"] == 0 for i in info), (order, info)
+    tol_f = TOL[precision] * (1 if precision == 0 else 10)
+    for order in (3, 4):
+        D = H.effective(order)
+        assert rel_err(D, G.D[order + 1]) < TOL_EFF[precision] * 10, order
+        Ks = multisets(order)
+        for L in (0, len(Ks) + 3, 6 * len(Ks) - 1):
+            a, k = divmod(L, len(Ks))
+            ref = tensor_to_mandel(G.eps[order + 1][(a, Ks[k])])
+            assert rel_err(H.field(order, L), ref) < tol_f, (order, L)
+    H.close()
+
+
+def test_order3_vanishes_for_centrosymmetric_cell():
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(16)
+    H = hom.Homogenization(ms, precision=0)
+    for order in range(4):
+        info = H.solve(order, 1e-12)
+        assert all(i["status"] == 0 for i in info)
+    assert np.abs(H.effective(3)).max() < 1e-9 * np.abs(H.effective(2)).max()
+    assert np.abs(H.effective(2)).max() > 1e-4
+    H.close()

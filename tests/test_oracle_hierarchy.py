@@ -84,3 +84,60 @@ def test_order2_nonzero_for_asymmetric_cell_and_homogeneous_zero():
     hh = Hierarchy(hom, tol=1e-11)
     hh.order1()
     assert np.abs(hh.order2()).max() < 1e-12
+
+
+# --- any order: the monomial-load builder ----------------------------------------------------
+
+def _asym_small():
+    from tests.helpers import random_phase
+    g = (6, 4, 4)
+    return synthetic.Microstructure(random_phase(g, 3, 21, p=[0.5, 0.3, 0.2]),
+                                    np.array([[1.0, 1.0], [6.0, 4.0], [0.3, 0.2]]), 3.0, 2.0)
+
+
+def test_monomial_derivatives():
+    from oracle.hierarchy import derivative_value, monomial, multisets
+    assert [len(multisets(d)) for d in range(5)] == [1, 3, 6, 10, 15]
+    # d^K (Y^K / K!) = 1, and any other derivative of the same degree vanishes
+    for K in multisets(3):
+        for J in multisets(3):
+            v = derivative_value(monomial(K), list(J))
+            assert v == (1.0 if J == K else 0.0), (K, J, v)
+    assert derivative_value(monomial((0, 0, 1)), [0]) is None   # still depends on Y
+
+
+def test_general_builder_reproduces_orders_2_and_3():
+    """The monomial-load builder gives the explicit alpha = 2 and alpha = 3 problems."""
+    from oracle.hierarchy import GeneralHierarchy, multisets
+    from oracle.tensors import MANDEL_PAIRS
+    ms = _asym_small()
+    h = Hierarchy(Problem(ms.phase, ms.lame, ms.lam0, ms.mu0), tol=1e-12)
+    h.order1()
+    h.order2()
+    h.order3()
+    G = GeneralHierarchy(h)
+    np.testing.assert_allclose(G.solve(2), h.d1, rtol=0, atol=1e-13)
+    idx = [6 * a + [i for i, pr in enumerate(MANDEL_PAIRS) if tuple(sorted(pr)) == K][0]
+           for a in range(6) for K in multisets(2)]
+    np.testing.assert_allclose(G.solve(3), h.d2[:, idx], rtol=0, atol=1e-13)
+
+
+def test_order4_vanishes_for_centrosymmetric_cell_and_homogeneous_zero():
+    """alpha = 4: the corrector is even for a centrosymmetric cell, so D_3 = 0 (as D_1); a
+    homogeneous medium has zero correctors at every order."""
+    from oracle.hierarchy import GeneralHierarchy
+    ms = synthetic.centred_sphere(6)
+    h = Hierarchy(Problem(ms.phase, ms.lame, ms.lam0, ms.mu0), tol=1e-12)
+    h.order1()
+    G = GeneralHierarchy(h)
+    G.solve(2)
+    d3 = G.solve(3)
+    d4 = G.solve(4)
+    assert np.abs(d3).max() > 1e-3
+    assert np.abs(d4).max() < 1e-12 * np.abs(d3).max() * 1e3
+    hom_ms = synthetic.Microstructure(np.zeros((4, 4, 4), np.uint8), np.array([[2.0, 1.0]]), 2.0, 1.0)
+    h = Hierarchy(Problem(hom_ms.phase, hom_ms.lame, hom_ms.lam0, hom_ms.mu0), tol=1e-12)
+    h.order1()
+    G = GeneralHierarchy(h)
+    for a in (2, 3, 4):
+        assert np.abs(G.solve(a)).max() == 0.0
