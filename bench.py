@@ -211,7 +211,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_1712_05145_gb300 import build, hom, synthetic
+    from paper_1712_05145_gb300 import build, hom, replicas, synthetic
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
@@ -271,13 +271,8 @@ def main():
     total_ms = ev[0].elapsed_time(ev[-1])
     worst = [i["rel_residual_fp64"] for i in info]
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    vi = torch.tensor([float(M) * iters], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(vi, op=dist.ReduceOp.SUM)
-    total_ms = float(t.item())
-    value = float(vi.item()) / (total_ms / 1e3)
+    total_ms, job_vi = replicas.aggregate(total_ms, float(M) * iters, device="cuda")
+    value = job_vi / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers: create from host arrays, solve, read C_eff
     e2e = None
@@ -294,7 +289,10 @@ def main():
             e2e_iters += sum(i["iterations"] for i in inf)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": M * e2e_iters / e2e_s * world, "unit": "voxel-iters/s",
+        if dist is not None:
+            dist.barrier()
+        e2e = {"value": replicas.job_rate(e2e_s * 1e3, float(M) * e2e_iters, device="cuda"),
+               "unit": "voxel-iters/s",
                "h2d_bytes_per_step": int(M + ms.lame.nbytes), "d2h_bytes_per_step": 6 * 6 * 8,
                "steps": max(1, args.steps // 2),
                "note": "hom_create from host phase/Lame arrays + hom_solve + hom_effective to host + hom_destroy"}

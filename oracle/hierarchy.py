@@ -34,9 +34,16 @@ Readings (the paper is silent or garbled here):
   unit load, D[:, load] = < C : eps_alpha + p_alpha > (Mandel), which the paper leaves
   for future work.
 
+Any order alpha >= 2 (``GeneralHierarchy``): the unit loads are E^A m_K(Y) with m_K = Y^K / K!
+for the multisets K of alpha - 1 directions; p_alpha and g_alpha are sums over the order
+alpha - 1 correctors with the coefficients d_j d^J m_K, computed by differentiating the
+monomial.
+
 Pins (tests/test_oracle_hierarchy.py): i theta_hat xi = g_hat; the displacement /
-strain round trip; linearity; D_1 = 0 for centrosymmetric cells.  Beyond these the
-alpha = 2 and alpha = 3 builders are "parity unpinned": the paper prints no value for them.
+strain round trip; linearity; D_1 = 0 for centrosymmetric cells; the general builder
+reproduces the explicit alpha = 2 and alpha = 3 builders; D_3 = 0 (alpha = 4) for
+centrosymmetric cells; zero correctors at every order for a homogeneous medium.  Beyond these
+the values of alpha >= 3 are "parity unpinned": the paper prints no value for them.
 """
 import numpy as np
 
