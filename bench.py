@@ -200,7 +200,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--rhs-chunk", type=int, default=0,
                     help="loads transformed per launch (0: as many as fit the spectrum budget)")
-    ap.add_argument("--l2-budget-mb", type=int, default=128, help="spectrum scratch budget")
+    ap.add_argument("--spectrum-budget-mb", type=int, default=1024, help="spectrum scratch budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -227,7 +227,7 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, scheme=hom.HOM_CG, stream=stream.cuda_stream,
-                           rhs_chunk=args.rhs_chunk, l2_budget_bytes=args.l2_budget_mb << 20)
+                           rhs_chunk=args.rhs_chunk, spectrum_budget_bytes=args.spectrum_budget_mb << 20)
 
     def step():
         info = H.solve(0, TOL)
@@ -323,7 +323,7 @@ def main():
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [n, n, n], "loads": 6, "tol": TOL, "seed": SEED,
-                   "rhs_chunk": args.rhs_chunk, "l2_budget_mb": args.l2_budget_mb,
+                   "rhs_chunk": args.rhs_chunk, "spectrum_budget_mb": args.spectrum_budget_mb,
                    "l2": "inputs larger than L2 (x, r, p fields 302 MB each)", "parallelism": "replicas"},
         "solves_per_s": world * args.steps / (total_ms / 1e3),
         "p50_ms": float(np.percentile(step_ms, 50)),

@@ -73,8 +73,10 @@ typedef struct {
   int32_t check_every;     /* iterations between host convergence checks (>= 1) */
   int32_t max_refine;      /* FP32_REFINE: cap on FP64 residual-correction sweeps */
   int32_t rhs_chunk;       /* loads whose spectra are transformed per launch; 0 = choose so
-                              that the spectrum scratch fits l2_budget_bytes */
-  int64_t l2_budget_bytes; /* target size of the spectrum scratch (0 = 128 MiB) */
+                              that the spectrum scratch fits spectrum_budget_bytes */
+  int64_t spectrum_budget_bytes; /* target size of the spectrum scratch (0 = 1 GiB).  More loads
+                              per launch give the latency-bound kernels more CTAs; at 128^3 FP32
+                              the default transforms all 6 unit loads per launch */
   void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
   int32_t pass_mode;       /* x-y transforms: 0 = fused plane kernels when a plane fits one CTA,
                               else split x and y passes; 1 = always fused (fails if a plane does
@@ -92,7 +94,7 @@ typedef struct {
 } hom_solve_info;
 
 /* Fills *opt with defaults: HOM_FP32_REFINE, HOM_CG, max_iter 2000, check_every 8,
- * max_refine 6, rhs_chunk 0, l2_budget_bytes 128 MiB, own stream. */
+ * max_refine 6, rhs_chunk 0, spectrum_budget_bytes 1 GiB, own stream. */
 HOM_API void hom_default_options(hom_options* opt);
 
 /* Creates a handle for one voxel RVE (Sec. 2: C(x) piecewise isotropic, reference C0).

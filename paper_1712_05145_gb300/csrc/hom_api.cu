@@ -1076,7 +1076,7 @@ HOM_API void hom_default_options(hom_options* opt) {
   opt->check_every = 8;
   opt->max_refine = 6;
   opt->rhs_chunk = 0;
-  opt->l2_budget_bytes = 128LL << 20;
+  opt->spectrum_budget_bytes = 1024LL << 20;
   opt->cuda_stream = nullptr;
 }
 
@@ -1109,7 +1109,7 @@ HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t
     return -1;
   const bool fp32 = (precision == HOM_FP32_REFINE);
   const long long M = n1 * n2 * n3, plane_c = n2 * (n1 / 2 + 1);
-  const long long budget = 128LL << 20;
+  const long long budget = 1024LL << 20;
   auto scratch = [&](long long elem) {
     const long long per = 6 * n3 * plane_c * elem;
     long long chunk = std::max(1LL, budget / per);
@@ -1199,7 +1199,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if (c->opt.max_iter < 1) c->opt.max_iter = 1;
   if (c->opt.check_every < 1) c->opt.check_every = 1;
   if (c->opt.max_refine < 0) c->opt.max_refine = 0;
-  if (c->opt.l2_budget_bytes <= 0) c->opt.l2_budget_bytes = 128LL << 20;
+  if (c->opt.spectrum_budget_bytes <= 0) c->opt.spectrum_budget_bytes = 1024LL << 20;
   if (c->opt.precision != HOM_FP64 && c->opt.precision != HOM_FP32_REFINE) { delete c; return HOM_ERR_ARG; }
   if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG && c->opt.scheme != HOM_BICGSTAB) {
     delete c;
@@ -1291,7 +1291,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   // spectrum scratch
   const size_t elem = c->fp32 ? sizeof(cx<float>) : sizeof(cx<double>);
   c->S_rhs_bytes = (size_t)6 * n3 * (size_t)g.plane_c * elem;
-  const size_t budget = (size_t)c->opt.l2_budget_bytes;
+  const size_t budget = (size_t)c->opt.spectrum_budget_bytes;
   c->chunk = c->opt.rhs_chunk > 0 ? c->opt.rhs_chunk : (int)std::max<size_t>(1, budget / c->S_rhs_bytes);
   c->chunk = std::min(c->chunk, 64);
   c->S_comps = std::max(6 * c->chunk, 9);

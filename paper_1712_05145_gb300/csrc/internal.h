@@ -17,7 +17,6 @@ struct Geo {
   int P;                 // shared-memory row pitch of a plane (complex elements, odd)
   long long M;           // voxels
   long long plane_c;     // n2 * (h + 1)
-  int thr_plane;         // threads per CTA of the plane kernels
   FastDiv fd_h, fd_n2;   // division by h and n2 (pencil counts of the column and row FFTs)
   // split passes (grids whose x-y plane does not fit one CTA, or by choice):
   int split;             // 1: x pass + y pass kernels instead of the fused plane kernels
@@ -162,7 +161,7 @@ cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s);
 
 size_t plane_smem_bytes(const Geo& g, size_t elem);
 size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2);
-// fills fd_h, fd_n2 and thr_plane of a geometry whose n1, n2, n3 are set
+// fills fd_h, fd_n2 and the split-pass tiling of a geometry whose n1, n2, n3 are set
 void geo_finish(Geo& g);
 // resident CTAs per SM of the z pass for a launch shape (occupancy query, cached)
 template <typename T>

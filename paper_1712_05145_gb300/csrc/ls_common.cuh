@@ -19,9 +19,26 @@
 namespace hom {
 
 constexpr int kEPT = 16;
-// elements per thread whose global loads a plane kernel issues together in its prologue and
-// epilogue loops
-constexpr int kBatch = 4;
+// Launch shape of the plane kernels per compute precision.  FP32: 8 elements per thread,
+// CTAs of up to 1024 threads and 2 CTAs per SM (32 registers per thread, radices <= 8), which
+// keeps every warp slot of an SM busy on 128 x 64 planes.  FP64: 16 elements per thread, CTAs
+// of up to 512 threads.  kBatch: elements per thread whose global loads the prologue and
+// epilogue loops issue together; kSBatch: the same for the spectrum read of plane_inv.
+template <typename T> struct PlaneCfg;
+template <> struct PlaneCfg<float> {
+  static constexpr int kEPT = 8, kMaxThreads = 1024, kMinBlocks = 2, kBatch = 2, kSBatch = 4;
+};
+template <> struct PlaneCfg<double> {
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
+};
+// threads of a plane CTA: every element of the n2 x h plane has a slot, whole warps, >= 128
+template <typename T>
+inline int plane_threads(const Geo& g) {
+  const long long e = (long long)g.n2 * g.h;
+  int thr = (int)((e + PlaneCfg<T>::kEPT - 1) / PlaneCfg<T>::kEPT);
+  thr = ((thr + 31) / 32) * 32;
+  return thr < 128 ? 128 : thr;
+}
 // An FP32 Krylov sweep (state flag `stall`) whose residual has not halved for kStallIters
 // iterations ends (the FP64 residual sweep then restarts it, or reports non-convergence).
 // Below kNearFloor (relative residual) an FP32 sweep is close to its rounding floor and a

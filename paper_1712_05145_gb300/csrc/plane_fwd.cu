@@ -6,7 +6,9 @@ namespace hom {
 // ---------------------------------------------------------------------------------
 // plane_fwd: one CTA per (z-plane, component, rhs)
 template <typename Tf, typename T, int EPT>
-__global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) {
+__global__ void __launch_bounds__(PlaneCfg<T>::kMaxThreads, PlaneCfg<T>::kMinBlocks)
+plane_fwd_kernel(const FwdArgs<Tf, T> a) {
+  constexpr int kBatch = PlaneCfg<T>::kBatch;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Geo& g = a.g;
   const int z = blockIdx.x, c = blockIdx.y, lrhs = blockIdx.z, rhs = a.rhs0 + lrhs;
@@ -205,10 +207,6 @@ __global__ void __launch_bounds__(512) plane_fwd_kernel(const FwdArgs<Tf, T> a) 
 }
 
 void geo_finish(Geo& g) {
-  const long long e = (long long)g.n2 * g.h;
-  int thr = (int)((e + kEPT - 1) / kEPT);
-  thr = ((thr + 31) / 32) * 32;
-  g.thr_plane = thr < 128 ? 128 : (thr > 512 ? 512 : thr);
   g.fd_h = make_fastdiv((unsigned)g.h);
   g.fd_n2 = make_fastdiv((unsigned)g.n2);
   // split passes: x pass with rb rows of h values per CTA (<= kEPT * 256 elements),
@@ -290,15 +288,17 @@ template void zpass_tiling<double>(ZArgs<double>&);
 
 template <typename Tf, typename T>
 cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) {
-  if ((long long)a.g.n2 * a.g.h > (long long)kEPT * a.g.thr_plane || a.g.thr_plane > 512 || a.n_phase > 256)
+  const int thr = plane_threads<T>(a.g);
+  if ((long long)a.g.n2 * a.g.h > (long long)PlaneCfg<T>::kEPT * thr || thr > PlaneCfg<T>::kMaxThreads ||
+      a.n_phase > 256)
     return cudaErrorInvalidValue;
   const size_t smem = plane_smem_bytes(a.g, sizeof(cx<T>));
-  auto k = plane_fwd_kernel<Tf, T, kEPT>;
+  auto k = plane_fwd_kernel<Tf, T, PlaneCfg<T>::kEPT>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.n3, a.ncomp, nrhs);
   count_launch();
-  k<<<grid, a.g.thr_plane, smem, s>>>(a);
+  k<<<grid, thr, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -6,7 +6,9 @@ namespace hom {
 // ---------------------------------------------------------------------------------
 // plane_inv: one CTA per (z-plane, component, rhs)
 template <typename Tf, typename T, int EPT>
-__global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) {
+__global__ void __launch_bounds__(PlaneCfg<T>::kMaxThreads, PlaneCfg<T>::kMinBlocks)
+plane_inv_kernel(const InvArgs<Tf, T> a) {
+  constexpr int kBatch = PlaneCfg<T>::kBatch;
   const int s_ncomp = a.s_ncomp;
   const T c0h = a.c0h, c0d = a.c0d;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
   const int nmain = n2 * h;
   // the spectrum plane is contiguous (row pitch h): flat index e = row * h + col; kSBatch
   // loads of a thread are in flight together
-  constexpr int kSBatch = 8;
+  constexpr int kSBatch = PlaneCfg<T>::kSBatch;
   for (int e0 = tid; e0 < nmain; e0 += kSBatch * nthr) {
     cx<T> v[kSBatch];
     #pragma unroll
@@ -187,15 +189,16 @@ __global__ void __launch_bounds__(512) plane_inv_kernel(const InvArgs<Tf, T> a) 
 
 template <typename Tf, typename T>
 cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s) {
-  if ((long long)a.g.n2 * a.g.h > (long long)kEPT * a.g.thr_plane || a.g.thr_plane > 512)
+  const int thr = plane_threads<T>(a.g);
+  if ((long long)a.g.n2 * a.g.h > (long long)PlaneCfg<T>::kEPT * thr || thr > PlaneCfg<T>::kMaxThreads)
     return cudaErrorInvalidValue;
   const size_t smem = plane_smem_bytes(a.g, sizeof(cx<T>));
-  auto k = plane_inv_kernel<Tf, T, kEPT>;
+  auto k = plane_inv_kernel<Tf, T, PlaneCfg<T>::kEPT>;
   cudaError_t e = set_smem(k, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.g.n3, a.ncomp, nrhs);
   count_launch();
-  k<<<grid, a.g.thr_plane, smem, s>>>(a);
+  k<<<grid, thr, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
     python -m paper_1712_05145_gb300.hashin2d grid       # iterations and times against n (Fig. 3, Table 1)
     python -m paper_1712_05145_gb300.hashin2d contrast   # iterations against E2 / E1 at 64^2 (Fig. 4)
     python -m paper_1712_05145_gb300.hashin2d bulk       # in-plane bulk modulus against the matrix's
+    python -m paper_1712_05145_gb300.hashin2d fields --out DIR   # the displacement fields of Fig. 2
 
 Problems, as in Sec. 4 (the paper's numbering):
 * first-order problem: the cell problem for E = Id (in-plane: E11 = E22 = 1);
@@ -104,9 +105,33 @@ def in_plane_bulk_modulus(sizes):
         H.close()
 
 
+def displacement_fields(n, out_dir):
+    """The fields Fig. 2 shows, as arrays: the first displacement component of the first-order
+    problem (E = Id) and of the second-order problem ((grad E)_111 = (grad E)_222 = 1) on the n x n
+    Hashin structure, written to out_dir/hashin2d_fig2_n{n}.npz (arrays u1_first, u1_second, shape
+    n x n, index [y2][y1])."""
+    import os
+    from paper_1712_05145_gb300 import hom, synthetic
+    ms = synthetic.hashin_2d(n)
+    H = hom.Homogenization(ms, precision=hom.HOM_FP64, scheme=hom.HOM_CG)
+    H.solve(0, TOL, loads=E_ID)
+    u_first = H.field(0, 0, hom.HOM_FIELD_DISPLACEMENT)[0, 0]
+    H.solve(0, TOL, loads=np.eye(6)[[0, 1]])
+    H.solve(1, TOL, loads=W_111_222)
+    u_second = H.field(1, 0, hom.HOM_FIELD_DISPLACEMENT)[0, 0]
+    H.close()
+    os.makedirs(out_dir, exist_ok=True)
+    path = os.path.join(out_dir, "hashin2d_fig2_n%d.npz" % n)
+    np.savez(path, u1_first=u_first, u1_second=u_second)
+    print(json.dumps({"experiment": "Hashin 2-D displacement fields (Fig. 2)", "n": n, "file": path,
+                      "u1_first_range": [float(u_first.min()), float(u_first.max())],
+                      "u1_second_range": [float(u_second.min()), float(u_second.max())]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("experiment", choices=["grid", "contrast", "bulk"])
+    ap.add_argument("experiment", choices=["grid", "contrast", "bulk", "fields"])
+    ap.add_argument("--out", type=str, default="hashin2d_out")
     ap.add_argument("--sizes", type=str, default="8,16,32,64,128,256,512")
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--max-iter", type=int, default=100000)
@@ -118,6 +143,8 @@ def main():
         run_grid(sizes, args.max_iter)
     elif args.experiment == "contrast":
         run_contrast(args.n, [10.0 ** e for e in np.arange(-4.0, 4.01, 1.0)], args.max_iter)
+    elif args.experiment == "fields":
+        displacement_fields(128, args.out)
     else:
         in_plane_bulk_modulus(sizes)
 

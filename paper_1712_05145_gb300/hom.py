@@ -52,7 +52,7 @@ EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "
 class hom_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("scheme", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
-                ("l2_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
+                ("spectrum_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("pass_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
@@ -373,7 +373,7 @@ class Homogenization:
     NLOADS = {0: 6, 1: 18, 2: 36}
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
-                 max_refine=6, rhs_chunk=0, l2_budget_bytes=128 << 20, stream=None, lam0=None, mu0=None,
+                 max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,
                  pass_mode=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
@@ -385,7 +385,7 @@ class Homogenization:
         opt.check_every = check_every
         opt.max_refine = max_refine
         opt.rhs_chunk = rhs_chunk
-        opt.l2_budget_bytes = l2_budget_bytes
+        opt.spectrum_budget_bytes = spectrum_budget_bytes
         opt.cuda_stream = stream
         opt.pass_mode = pass_mode
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,

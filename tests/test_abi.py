@@ -72,3 +72,11 @@ def test_null_handle_calls(lib):
     assert lib.hom_effective(None, 0, None) == hom.HOM_ERR_ARG
     assert lib.hom_device_bytes(None) == 0
     lib.hom_destroy(None)
+
+
+def test_estimate_accepts_two_dimensional_cells_and_rejects_empty_axes(lib):
+    assert hom.hom_estimate_bytes((64, 64, 1), 0) > 0
+    assert hom.hom_estimate_bytes((64, 64, 1), 4) > hom.hom_estimate_bytes((64, 64, 1), 3)
+    for g in [(0, 8, 8), (8, 0, 8), (8, 8, 0), (8, 1, 8), (1, 8, 8)]:
+        assert hom.hom_estimate_bytes(g, 0) < 0
+    assert hom.hom_estimate_bytes((8, 8, 8), 5) < 0

@@ -142,3 +142,19 @@ def test_bicgstab_high_contrast_three_phases(precision):
     for a in (0, 5):
         assert rel_err(H.field(0, a), ref_f[a]) < (1e-8 if precision == 0 else 1e-4), a
     H.close()
+
+
+@pytest.mark.parametrize("precision,scheme", [(0, 1), (1, 1), (0, 2), (0, 0)])
+def test_zero_load_is_exact_and_free(precision, scheme):
+    """A zero macroscopic strain has b = 0: the solution 0 is exact, with no iteration."""
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.random_spheres((16, 16, 16), seed=9)
+    H = hom.Homogenization(ms, precision=precision, scheme=scheme)
+    loads = np.zeros((2, 6))
+    loads[1, 0] = 1.0
+    info = H.solve(0, 1e-8, loads=loads)
+    assert info[0]["status"] == 0 and info[0]["iterations"] <= (1 if scheme == 0 else 0)
+    assert np.abs(H.field(0, 0)).max() == 0.0
+    assert np.abs(H.effective(0)[:, 0]).max() == 0.0
+    assert info[1]["status"] == 0 and info[1]["iterations"] > 0
+    H.close()
