@@ -285,51 +285,26 @@ __device__ __forceinline__ void fft_pencils(cx<T>* buf, const Addr& addr, int n,
                                             const cx<T>* tw) {
 #define HOM_SEQ(NN, ...) \
   case NN: StageSeq<T, DIR, EPT, NN, 1, __VA_ARGS__>::run(buf, addr, npen, npd, tw); break;
-  if constexpr (EPT <= 8) {
-    // at most 8 elements per thread: radices <= 8 (more stages, fewer live registers)
-    switch (n) {
-      case 1: break;  // a single plane along z (two-dimensional cells): the identity
-      HOM_SEQ(2, 2)
-      HOM_SEQ(3, 3)
-      HOM_SEQ(4, 4)
-      HOM_SEQ(6, 6)
-      HOM_SEQ(8, 8)
-      HOM_SEQ(12, 4, 3)
-      HOM_SEQ(16, 8, 2)
-      HOM_SEQ(24, 8, 3)
-      HOM_SEQ(32, 8, 4)
-      HOM_SEQ(48, 8, 6)
-      HOM_SEQ(64, 8, 8)
-      HOM_SEQ(96, 8, 4, 3)
-      HOM_SEQ(128, 8, 4, 4)
-      HOM_SEQ(192, 8, 8, 3)
-      HOM_SEQ(256, 8, 8, 4)
-      HOM_SEQ(384, 8, 8, 6)
-      HOM_SEQ(512, 8, 8, 8)
-      default: break;
-    }
-  } else {
-    switch (n) {
-      case 1: break;  // a single plane along z (two-dimensional cells): the identity
-      HOM_SEQ(2, 2)
-      HOM_SEQ(3, 3)
-      HOM_SEQ(4, 4)
-      HOM_SEQ(6, 6)
-      HOM_SEQ(8, 8)
-      HOM_SEQ(12, 12)
-      HOM_SEQ(16, 16)
-      HOM_SEQ(24, 8, 3)
-      HOM_SEQ(32, 8, 4)
-      HOM_SEQ(48, 16, 3)
-      HOM_SEQ(64, 16, 4)
-      HOM_SEQ(96, 16, 6)
-      HOM_SEQ(128, 16, 8)
-      HOM_SEQ(192, 16, 12)
-      HOM_SEQ(256, 16, 16)
-      HOM_SEQ(384, 16, 8, 3)
-      HOM_SEQ(512, 8, 8, 8)
-      default: break;
-    }
+  switch (n) {
+    case 1: break;  // a single plane along z (two-dimensional cells): the identity
+    HOM_SEQ(2, 2)
+    HOM_SEQ(3, 3)
+    HOM_SEQ(4, 4)
+    HOM_SEQ(6, 6)
+    HOM_SEQ(8, 8)
+    HOM_SEQ(12, 12)
+    HOM_SEQ(16, 16)
+    HOM_SEQ(24, 8, 3)
+    HOM_SEQ(32, 8, 4)
+    HOM_SEQ(48, 16, 3)
+    HOM_SEQ(64, 16, 4)
+    HOM_SEQ(96, 16, 6)
+    HOM_SEQ(128, 16, 8)
+    HOM_SEQ(192, 16, 12)
+    HOM_SEQ(256, 16, 16)
+    HOM_SEQ(384, 16, 8, 3)
+    HOM_SEQ(512, 8, 8, 8)
+    default: break;
   }
 #undef HOM_SEQ
 }

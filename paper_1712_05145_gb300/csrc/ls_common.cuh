@@ -19,14 +19,14 @@
 namespace hom {
 
 constexpr int kEPT = 16;
-// Launch shape of the plane kernels per compute precision.  FP32: 8 elements per thread,
-// CTAs of up to 1024 threads and 2 CTAs per SM (32 registers per thread, radices <= 8), which
-// keeps every warp slot of an SM busy on 128 x 64 planes.  FP64: 16 elements per thread, CTAs
-// of up to 512 threads.  kBatch: elements per thread whose global loads the prologue and
-// epilogue loops issue together; kSBatch: the same for the spectrum read of plane_inv.
+// Launch shape of the plane kernels per compute precision: 16 elements per thread, CTAs of up
+// to 512 threads.  (8 elements per thread with 1024-thread CTAs and 32 registers, which doubles
+// the resident warps, measured slower at 128^3: the extra radix stage and register spills cost
+// more than the occupancy gained.)  kBatch: elements per thread whose global loads the prologue
+// and epilogue loops issue together; kSBatch: the same for the spectrum read of plane_inv.
 template <typename T> struct PlaneCfg;
 template <> struct PlaneCfg<float> {
-  static constexpr int kEPT = 8, kMaxThreads = 1024, kMinBlocks = 2, kBatch = 2, kSBatch = 4;
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
 };
 template <> struct PlaneCfg<double> {
   static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;

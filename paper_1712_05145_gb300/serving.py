@@ -4,9 +4,10 @@ Requests draw a grid from {32, 48, 64, 96, 128}^3 plus 32 x 64 x 128, order 0 or
 probability 1/2, and a random-sphere microstructure (volume fraction 0.3, radii 4-10 voxels of a
 128 grid) whose inclusion/matrix stiffness contrast is log-uniform in [2, 1000] (nu = 0.3).
 Geometries come from a seeded pool of a few per grid (the contrast is drawn per request).
-Arrivals are Poisson at a rate of 0.8 x the capacity measured on a back-to-back batch (or
---rate).  The server (FP32 fields, FP64 reductions and refinement) admits requests by free
-device memory; the comparison is the plain FP64 form, one request after the other.
+Arrivals are Poisson at a rate of 0.8 x the capacity measured on a back-to-back batch of the
+first --capacity-requests requests (or --rate).  The server (FP32 fields, FP64 reductions and
+refinement) admits requests by free device memory; the comparison is the plain FP64 form, one
+request after the other.
 
     python -m paper_1712_05145_gb300.serving --requests 2000
 """
@@ -66,6 +67,7 @@ def main():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=0.0, help="arrivals per second (0: 0.8 x measured capacity)")
     ap.add_argument("--max-active", type=int, default=6)
+    ap.add_argument("--capacity-requests", type=int, default=200)
     ap.add_argument("--pool", type=int, default=3)
     ap.add_argument("--baseline-requests", type=int, default=60)
     ap.add_argument("--tol", type=float, default=1e-6)
@@ -77,8 +79,9 @@ def main():
     build.build()
     grids, pool = build_pool(args.pool, args.seed)
     reqs = make_requests(args.requests, grids, pool, args.seed)
-    # capacity: a back-to-back batch (all submitted at once)
-    cap_n = min(40, len(reqs))
+    # capacity: a back-to-back batch (all submitted at once), long enough to see the grid and
+    # order mix rather than its first few draws
+    cap_n = min(args.capacity_requests, len(reqs))
     res, wall = run_stream(reqs[:cap_n], 0.0, args.max_active, args.tol, args.seed)
     capacity = cap_n / wall
     rate = args.rate if args.rate > 0 else 0.8 * capacity
