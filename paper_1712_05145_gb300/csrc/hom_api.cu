@@ -537,11 +537,12 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   // the FP64 residual they restart from.
   const double kSweepGain = 1e-5, kFirstSweepFloor = 3e-7;
   const double tol_inner = (mixed && !basic) ? std::max(0.5 * tol, kFirstSweepFloor) : (mixed ? 0.5 * tol : tol);
-  // The FP32 corrections leave incompatible rounding noise in x of ~1e-7 relative; it enters the
-  // FP64 residual at that level.  Below tol 1e-6 the residual sweeps therefore run on the
-  // projected x (one more FP64 pass per sweep); at looser tolerances the noise is under tol/10.
-  const double kProjectBelow = 1e-6;
-  const bool project = mixed && tol < kProjectBelow;
+  // The FP32 corrections leave an incompatible part in x: CG's step lengths reach C0 / C_min
+  // along the soft phases' directions and multiply the FP32 rounding of each direction p by as
+  // much (4.4e-5 of ||b|| at 128^3 and contrast 100).  The residual form b - Gamma0 * (C : x)
+  // does not see it, but the operator of Eq. cg_form does.  Every FP64 residual sweep therefore
+  // runs on the projected x (one more FP64 pass per sweep), which makes the two forms agree.
+  const bool project = mixed;
 
   std::vector<RhsState> st(n);
   for (int i = 0; i < n; ++i) {

@@ -25,8 +25,8 @@ constexpr int kEPT = 16;
 // more than the occupancy gained.)  kBatch: elements per thread whose global loads the prologue
 // and epilogue loops issue together; kSBatch: the same for the spectrum read of plane_inv.
 template <typename T> struct PlaneCfg;
-template <> struct PlaneCfg<float> {
-  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
+template <> struct PlaneCfg<float> {   // 64 registers: 2 CTAs per SM
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 2, kBatch = 4, kSBatch = 8;
 };
 template <> struct PlaneCfg<double> {
   static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
