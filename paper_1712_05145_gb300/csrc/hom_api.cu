@@ -511,6 +511,27 @@ hom_status bicgstab_sweep(hom_ctx* c, int n, Tf* x, Tf* r, Tf* p, std::vector<Rh
   return HOM_OK;
 }
 
+// FP64 residual of the operator of Eq. cg_form itself, r = b - A x with A = Id + Gamma0 * (C - C0):
+// one LS pass, tau = (C - C0) : (x + E), r = -Gamma0 * tau + b - x (for order 0, b is the E term
+// inside tau).  Unlike residual_sweep it sees an incompatible part of x, so a value below tol
+// certifies the solution without a projection.
+template <typename Tf>
+hom_status literal_residual(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
+                            const std::vector<int>* act) {
+  auto fa = fwd_args<double, double>(c, FWD_TAU, 6, 6);
+  fa.in = x64;
+  fa.E = dE;
+  fa.st = c->d_st;
+  auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+  za.st = c->d_st;
+  auto ia = inv_args<Tf, double>(c, INV_STORE, FIN_RESID, 6, 6, 6);
+  ia.out = r;
+  ia.b = b64;
+  ia.xsub = x64;
+  ia.st = c->d_st;
+  return ls_pass<double, Tf, double>(c, n, fa, za, ia, act);
+}
+
 // Solves A x = b (Eq. cg_form) for n loads; b = -Gamma0 * (C : E) for Kelvin loads dE (order 0,
 // device [n][6]) or b = b64 (higher orders).  The solution x64 is FP64 in both precisions.
 //  FP64 mode (Tf = double): Basic Scheme or CG in FP64 directly on x64.
@@ -535,13 +556,18 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   // The first sweep starts from b and aims at the tolerance itself where FP32 can reach it
   // (relative residuals down to kFirstSweepFloor); later sweeps ask for kSweepGain relative to
   // the FP64 residual they restart from.
-  const double kSweepGain = 1e-5, kFirstSweepFloor = 3e-7;
-  const double tol_inner = (mixed && !basic) ? std::max(0.5 * tol, kFirstSweepFloor) : (mixed ? 0.5 * tol : tol);
+  const double kSweepGain = 1e-5, kFirstSweepTarget = 1e-4;
+  const double tol_inner = (mixed && !basic) ? std::max(0.5 * tol, kFirstSweepTarget) : (mixed ? 0.5 * tol : tol);
   // The FP32 corrections leave an incompatible part in x: CG's step lengths reach C0 / C_min
   // along the soft phases' directions and multiply the FP32 rounding of each direction p by as
   // much (4.4e-5 of ||b|| at 128^3 and contrast 100).  The residual form b - Gamma0 * (C : x)
-  // does not see it, but the operator of Eq. cg_form does.  Every FP64 residual sweep therefore
-  // runs on the projected x (one more FP64 pass per sweep), which makes the two forms agree.
+  // does not see it, but the operator of Eq. cg_form does.  So in FP32 mode:
+  //  * a sweep that aimed at the tolerance is verified with the literal residual b - A x (one
+  //    FP64 pass, which sees the incompatible part); below tol the load is done;
+  //  * otherwise x is projected onto compatible fields and CG restarts from the residual of the
+  //    projected x (two FP64 passes).  The first sweep aims only at kFirstSweepTarget: the
+  //    projection after it perturbs the residual by about the incompatible part anyway, and the
+  //    later sweeps, whose corrections are small, leave a negligible incompatible part.
   const bool project = mixed;
 
   std::vector<RhsState> st(n);
@@ -613,8 +639,8 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
     for (int i = 0; i < n; ++i) st[i].active = 1;
     CKS(write_states(c, st));
     std::vector<int> all(n, 1);
-    if (project) CKS(project_compatible(c, n, x64, &all));
-    CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &all));
+    if (mixed) CKS(literal_residual<Tf>(c, n, dE, b64, x64, r, &all));   // sees an incompatible part
+    else CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &all));
     CKS(read_states(c, n, st));
     for (int i = 0; i < n; ++i) {
       st[i].res = before[i].res;
@@ -691,7 +717,33 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
       }
       if (!need) break;
       CKS(write_states(c, st));
-      if (project) CKS(project_compatible(c, n, x64, &act));
+      if (project) {
+        // loads whose sweep aimed at the tolerance: the literal residual decides
+        std::vector<int> check(n, 0);
+        bool any_check = false;
+        for (int i = 0; i < n; ++i) {
+          check[i] = act[i] && st[i].tol <= tol;
+          any_check = any_check || check[i];
+        }
+        if (any_check) {
+          for (int i = 0; i < n; ++i) st[i].active = check[i];
+          CKS(write_states(c, st));
+          CKS(literal_residual<Tf>(c, n, dE, b64, x64, r, &check));
+          CKS(read_states(c, n, st));
+          bool rest = false;
+          for (int i = 0; i < n; ++i) {
+            if (check[i] && st[i].res_true < tol) {
+              done[i] = 1;
+              act[i] = 0;
+            }
+            st[i].active = act[i];
+            rest = rest || act[i];
+          }
+          CKS(write_states(c, st));
+          if (!rest) break;
+        }
+        CKS(project_compatible(c, n, x64, &act));
+      }
       CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       CKS(read_states(c, n, st));
       bool again = false;

@@ -117,6 +117,7 @@ struct InvArgs {
   T out_scale;           // INV_STORE: out = out_scale * eta (+ b)
   Tf* out;               // INV_STORE
   const double* b;       // INV_STORE: added right-hand-side field, FP64 (nullable)
+  const double* xsub;    // INV_STORE: subtracted field, FP64 (nullable): out = scale*eta + b - xsub
   const Tf* prev;        // INV_STORE: previous iterate for the Cauchy difference (nullable)
   const Tf* p;           // INV_CG
   Tf* x;                 // INV_CG

@@ -38,6 +38,7 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
       } else {
         const long long fo = ((long long)(rhs * a.out_ncomp + c) * g.n3 + z) * psz;
         if (a.b != nullptr) prefetch_l2(a.b + fo, (unsigned)(psz * (long long)sizeof(double)));
+        if (a.xsub != nullptr) prefetch_l2(a.xsub + fo, (unsigned)(psz * (long long)sizeof(double)));
         if (a.fin == FIN_BASIC && a.prev != nullptr) prefetch_l2(a.prev + fo, pb);
       }
     }
@@ -52,6 +53,7 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
     long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
     long long b = fields * psz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>);
     if (a.b != nullptr) b += psz * (long long)sizeof(double);
+    if (a.xsub != nullptr) b += psz * (long long)sizeof(double);
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)psz);
   }
@@ -122,6 +124,7 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
         const cx<T> e = pl[row * P + c2];
         T v0 = a.out_scale * e.re, v1 = a.out_scale * e.im;
         if (a.b != nullptr) { double b0, b1; ld2<double>(a.b + o, b0, b1); v0 += (T)b0; v1 += (T)b1; }
+        if (a.xsub != nullptr) { double s0, s1; ld2<double>(a.xsub + o, s0, s1); v0 -= (T)s0; v1 -= (T)s1; }
         if (a.fin == FIN_BASIC) {
           Tf p0, p1;
           ld2<Tf>(a.prev + o, p0, p1);

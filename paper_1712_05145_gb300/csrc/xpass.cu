@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
     long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
     long long b = fields * vox * (long long)sizeof(Tf) + (long long)nr * h * (long long)sizeof(cx<T>);
     if (a.b != nullptr) b += vox * (long long)sizeof(double);
+    if (a.xsub != nullptr) b += vox * (long long)sizeof(double);
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)vox);
   }
@@ -213,6 +214,7 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
         const cx<T> e = pl[lr * P + c2];
         T v0 = a.out_scale * e.re, v1 = a.out_scale * e.im;
         if (a.b != nullptr) { double b0, b1; ld2<double>(a.b + o, b0, b1); v0 += (T)b0; v1 += (T)b1; }
+        if (a.xsub != nullptr) { double s0, s1; ld2<double>(a.xsub + o, s0, s1); v0 -= (T)s0; v1 -= (T)s1; }
         if (a.fin == FIN_BASIC) {
           Tf p0, p1;
           ld2<Tf>(a.prev + o, p0, p1);
