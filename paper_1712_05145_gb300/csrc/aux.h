@@ -12,6 +12,8 @@ cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int 
 cudaError_t launch_kelvin_to_mandel_inplace(double* f, long long M, int nf, cudaStream_t s);
 // x[i] += d[i] for i < n
 cudaError_t launch_add_correction(const float* d, double* x, long long n, cudaStream_t s);
+// x += a - b
+cudaError_t launch_add_difference(const float* a, const float* b, double* x, long long n, cudaStream_t s);
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long long n, cudaStream_t s);
 template <typename T>

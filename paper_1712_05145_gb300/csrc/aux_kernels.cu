@@ -112,6 +112,18 @@ cudaError_t launch_add_correction(const float* d, double* x, long long n, cudaSt
   return cudaGetLastError();
 }
 
+// x += a - b (FP64 solution moved by the difference of two FP32 fields: x <- x - (x32 - P x32))
+__global__ void add_difference_kernel(const float* __restrict__ a, const float* __restrict__ b, double* __restrict__ x,
+                                      long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += (double)a[i] - (double)b[i];
+}
+cudaError_t launch_add_difference(const float* a, const float* b, double* x, long long n, cudaStream_t s) {
+  count_launch();
+  add_difference_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, b, x, n);
+  return cudaGetLastError();
+}
+
 // ---- spectrum layouts ------------------------------------------------------------
 // internal: per plane, n2 rows of h values (kx < n1/2) then the n2 Nyquist values;
 // standard: [n3][n2][n1/2 + 1] complex.  basis: 0 keep, 1 Mandel->Kelvin, 2 Kelvin->Mandel
