@@ -81,7 +81,10 @@ typedef struct {
   int32_t pass_mode;       /* x-y transforms: 0 = fused plane kernels when a plane fits one CTA,
                               else split x and y passes; 1 = always fused (fails if a plane does
                               not fit); 2 = always split */
-  int32_t reserved[7];
+  int32_t autotune;        /* 1: before the first solve, time one operator application per
+                              candidate launch shape (loads per launch, z-pass tile width) on
+                              this grid and keep the fastest; 0 (default): fixed rules */
+  int32_t reserved[6];
 } hom_options;
 
 typedef struct {
@@ -276,6 +279,11 @@ HOM_API void hom_server_destroy(hom_server_t s);
 
 /* Bytes of device memory the handle holds now. */
 HOM_API int64_t hom_device_bytes(hom_t h);
+
+/* Launch shape of the handle's iteration passes: loads transformed per launch and the z-pass
+ * tile width as log2 of its columns (-1: chosen per launch by the occupancy rule).  After an
+ * autotuned solve these are the tuned values.  Pointers nullable. */
+HOM_API hom_status hom_launch_config(hom_t h, int32_t* loads_per_launch, int32_t* ztile_log2);
 
 /* Kernels this library has launched in this process so far, over all handles, servers and the
  * allocation-free entry point (a host-side count of launches issued, not of launches finished). */

@@ -98,6 +98,8 @@ struct hom_ctx {
   double* d_mout = nullptr;
   int mblk = 64;
   void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};
+  int ztile_lg[2] = {-1, -1};  // z-pass tile width forced by the autotuner (FP32, FP64); -1: rule
+  bool tuned = false;
   void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t
   size_t bicg_bytes = 0;
   size_t work_bytes[4] = {0, 0, 0, 0};
@@ -252,7 +254,7 @@ ZArgs<T> z_args(hom_ctx* c, int mode, int nin, int nout) {
   a.scale = 1.0 / (double)c->g.M;
   a.prof = c->prof_on ? c->d_prof + 2 * (HOM_KERNEL_ZPASS + (sizeof(T) == 8 ? 3 : 0)) : nullptr;
   a.tw_n3 = tw<T>(c, 3);
-  zpass_tiling<T>(a);
+  zpass_tiling<T>(a, c->ztile_lg[sizeof(T) == 8 ? 1 : 0]);
   return a;
 }
 template <typename Tf, typename T>
@@ -480,6 +482,63 @@ hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<i
   ia.out_scale = (Tf)-1;
   ia.st = c->d_st;
   return ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia, act);
+}
+
+// Autotuner (hom_options.autotune): times one operator application per candidate launch shape
+// on this handle's grid and keeps the fastest per load.  The candidates are the loads per launch
+// (1, 2, 3, 4, 6, 8, 12, ... up to the spectrum scratch's capacity, at most 12) and the z-pass
+// tile widths that fit (2^0 .. 2^4 columns).  It tunes the passes of the iteration precision T.
+template <typename T>
+hom_status autotune(hom_ctx* c) {
+  const int nt = std::min(c->chunk, 12);
+  std::vector<int> chunks;
+  for (int k : {1, 2, 3, 4, 6, 8, 12})
+    if (k <= nt) chunks.push_back(k);
+  std::vector<int> lgs;
+  for (int lg = 0; lg <= 4; ++lg)
+    if (zpass_tile_fits(c->g, sizeof(cx<T>), 6, lg)) lgs.push_back(lg);
+  if (lgs.empty()) return HOM_OK;
+  const size_t fb = tbytes<T>(c, nt, 6);
+  void *vin, *vout;
+  CKS(work(c, 0, fb, &vin));
+  CKS(work(c, 1, fb, &vout));
+  CK(cudaMemsetAsync(vin, 0, fb, c->stream));
+  CKS(ensure_cap(c, nt));
+  std::vector<RhsState> st(nt);
+  for (auto& s : st) {
+    s = RhsState{};
+    s.active = 1;
+  }
+  CKS(write_states(c, st));
+  const int chunk0 = c->chunk, idx = sizeof(T) == 8 ? 1 : 0;
+  cudaEvent_t e0 = pool_event(c), e1 = pool_event(c);
+  double best = 1e300;
+  int best_chunk = chunk0, best_lg = -1;
+  for (int ck : chunks) {
+    for (int lg : lgs) {
+      c->chunk = ck;
+      c->ztile_lg[idx] = lg;
+      CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));  // warm-up
+      CK(cudaEventRecord(e0, c->stream));
+      for (int rep = 0; rep < 2; ++rep)
+        CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_chunk = ck;
+        best_lg = lg;
+      }
+    }
+  }
+  c->ev_pool.push_back(e0);
+  c->ev_pool.push_back(e1);
+  c->chunk = best_chunk;
+  c->ztile_lg[idx] = best_lg;
+  c->tuned = true;
+  return HOM_OK;
 }
 
 // One BiCGSTAB sweep on A x = r from the current x (FP64 mode: the solution; FP32 mode: the
@@ -1183,6 +1242,13 @@ HOM_API const char* hom_last_error(hom_t h) { return h ? h->err.c_str() : "null 
 
 HOM_API int64_t hom_device_bytes(hom_t h) { return h ? (int64_t)h->bytes : 0; }
 
+HOM_API hom_status hom_launch_config(hom_t c, int32_t* loads_per_launch, int32_t* ztile_log2) {
+  if (!c) return HOM_ERR_ARG;
+  if (loads_per_launch) *loads_per_launch = c->chunk;
+  if (ztile_log2) *ztile_log2 = c->ztile_lg[c->fp32 ? 0 : 1];
+  return HOM_OK;
+}
+
 HOM_API int64_t hom_launch_count(void) { return hom::launch_counter().load(std::memory_order_relaxed); }
 
 HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision) {
@@ -1399,6 +1465,10 @@ HOM_API hom_status hom_solve(hom_t c, int32_t order, int32_t n_loads, const doub
   if (!(tol > 0.0)) return fail(c, HOM_ERR_ARG, "tol must be > 0");
   if (order < 0 || order > kMaxOrder) return fail(c, HOM_ERR_ARG, "order must be in 0..%d", kMaxOrder);
   for (int k = order + 1; k <= kMaxOrder; ++k) c->ord[k].solved = false;
+  if (c->opt.autotune && !c->tuned) {
+    hom_status t = c->fp32 ? autotune<float>(c) : autotune<double>(c);
+    if (t != HOM_OK) return t;
+  }
   if (order == 0) {
     int n = loads ? n_loads : 6;
     if (n < 1 || n > 64) return fail(c, HOM_ERR_ARG, "n_loads must be in 1..64");

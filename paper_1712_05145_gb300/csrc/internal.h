@@ -167,9 +167,12 @@ void geo_finish(Geo& g);
 // resident CTAs per SM of the z pass for a launch shape (occupancy query, cached)
 template <typename T>
 int zpass_ctas_per_sm(int threads, size_t smem);
-// z-pass tiling for ncomp input components: fills tc_log2, ntiles, nthr
+// z-pass tiling for ncomp input components: fills tc_log2, ntiles, nthr.  force_lg >= 0 asks for
+// tiles of 2^force_lg columns (used when it fits); otherwise the occupancy rule picks the width.
 template <typename T>
-void zpass_tiling(ZArgs<T>& a);
+void zpass_tiling(ZArgs<T>& a, int force_lg = -1);
+// whether tiles of 2^lg columns fit the z pass for ncomp input components (threads, shared memory)
+bool zpass_tile_fits(const Geo& g, size_t elem, int ncomp, int lg);
 
 // counts one kernel launch of this library (process-wide; read by hom_launch_count)
 void count_launch();

@@ -253,15 +253,20 @@ static int zpass_threads(int ncomp, int n3, int lg) {
   return thr < 128 ? 128 : thr;
 }
 
+bool zpass_tile_fits(const Geo& g, size_t elem, int ncomp, int lg) {
+  return lg >= 0 && lg <= 4 && (size_t)ncomp * g.n3 * ((size_t)1 << lg) <= (size_t)kEPT * 512 &&
+         zpass_smem_bytes(g, elem, ncomp, lg) <= 64 * 1024;
+}
+
 template <typename T>
-void zpass_tiling(ZArgs<T>& a) {
+void zpass_tiling(ZArgs<T>& a, int force_lg) {
   const size_t elem = sizeof(cx<T>);
   int best_lg = -1;
   long long best_warps = -1;
-  for (int lg = 4; lg >= 0; --lg) {
-    const bool fits = (size_t)a.ncomp_in * a.g.n3 * ((size_t)1 << lg) <= (size_t)kEPT * 512 &&
-                      zpass_smem_bytes(a.g, elem, a.ncomp_in, lg) <= 64 * 1024;
-    if (!fits) continue;
+  const bool forced = force_lg >= 0 && zpass_tile_fits(a.g, elem, a.ncomp_in, force_lg);
+  if (forced) best_lg = force_lg;
+  for (int lg = 4; lg >= 0 && !forced; --lg) {
+    if (!zpass_tile_fits(a.g, elem, a.ncomp_in, lg)) continue;
     if (best_lg >= 0 && ((size_t)1 << lg) * elem < 32) break;   // narrower than a sector
     const int thr = zpass_threads(a.ncomp_in, a.g.n3, lg);
     const long long warps =
@@ -283,8 +288,8 @@ void zpass_tiling(ZArgs<T>& a) {
   a.fd_comp = make_fastdiv((unsigned)(a.g.n3 * tc));
   a.nthr = zpass_threads(a.ncomp_in, a.g.n3, lg);
 }
-template void zpass_tiling<float>(ZArgs<float>&);
-template void zpass_tiling<double>(ZArgs<double>&);
+template void zpass_tiling<float>(ZArgs<float>&, int);
+template void zpass_tiling<double>(ZArgs<double>&, int);
 
 template <typename Tf, typename T>
 cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) {

@@ -45,15 +45,15 @@ EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "
             "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
             "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
             "hom_server_create", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
-            "hom_server_destroy", "hom_device_bytes", "hom_launch_count", "hom_last_error", "hom_status_string",
-            "hom_destroy"]
+            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_launch_count", "hom_last_error",
+            "hom_status_string", "hom_destroy"]
 
 
 class hom_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("scheme", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
                 ("spectrum_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("pass_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("pass_mode", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -154,6 +154,8 @@ def load_library(path=None):
     lib.hom_server_destroy.restype = None
     lib.hom_device_bytes.argtypes = [V]
     lib.hom_device_bytes.restype = I64
+    lib.hom_launch_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.hom_launch_config.restype = ctypes.c_int
     lib.hom_launch_count.argtypes = []
     lib.hom_launch_count.restype = I64
     lib.hom_last_error.argtypes = [V]
@@ -351,6 +353,13 @@ def hom_device_bytes(h):
     return int(load_library().hom_device_bytes(h))
 
 
+def hom_launch_config(h):
+    """(loads per launch, z-pass tile log2 width or -1) of a handle's iteration passes."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(h, load_library().hom_launch_config(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def hom_launch_count():
     """Kernels the library has launched in this process (host-side count)."""
     return int(load_library().hom_launch_count())
@@ -374,7 +383,7 @@ class Homogenization:
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
                  max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,
-                 pass_mode=0):
+                 pass_mode=0, autotune=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
         self.M = n1 * n2 * n3
@@ -388,6 +397,7 @@ class Homogenization:
         opt.spectrum_budget_bytes = spectrum_budget_bytes
         opt.cuda_stream = stream
         opt.pass_mode = pass_mode
+        opt.autotune = autotune
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
                             ms.mu0 if mu0 is None else mu0, opt)
         self.nloads = {}

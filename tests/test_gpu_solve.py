@@ -158,3 +158,22 @@ def test_zero_load_is_exact_and_free(precision, scheme):
     assert np.abs(H.effective(0)[:, 0]).max() == 0.0
     assert info[1]["status"] == 0 and info[1]["iterations"] > 0
     H.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_launch_shape_gives_identical_results(precision):
+    """The autotuner only changes loads per launch and z-pass tile width; per-load reductions keep
+    their order, so the solution is the same bits."""
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.random_spheres((32, 32, 32), seed=12)
+    out = []
+    for tune in (0, 1):
+        H = hom.Homogenization(ms, precision=precision, autotune=tune)
+        info = H.solve(0, 1e-8)
+        assert all(i["status"] == 0 for i in info)
+        chunk, lg = hom.hom_launch_config(H.h)
+        assert chunk >= 1 and (lg == -1) == (tune == 0)
+        out.append((H.effective(0), H.field(0, 2), [i["iterations"] for i in info]))
+        H.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
