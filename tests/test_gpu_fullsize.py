@@ -87,3 +87,22 @@ def test_voronoi_512_properties():
     assert np.abs(c - c.T).max() < 1e-5 * np.abs(c).max()
     assert between_bounds(c, [tuple(x) for x in ms.lame], fractions)
     H.close()
+
+
+def test_voronoi_128_solution_checked_by_oracle():
+    """The Voronoi microstructure of the 512^3 configuration on a 128^3 grid (same seeds): the
+    oracle recomputes the literal FP64 residual of the GPU solution for two loads."""
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.voronoi((128, 128, 128), seed=1716, n_grains=256)
+    H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, scheme=hom.HOM_CG)
+    info = H.solve(0, BENCH_TOL)
+    assert all(i["status"] == 0 for i in info), info
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    for a in (1, 4):
+        E = unit_mandel_load(a)
+        res = pb.residual(mandel_to_tensor(H.field(0, a)), pb.rhs(E))
+        assert res < BENCH_TOL, (a, res)
+    c = H.effective(0)
+    assert np.abs(c - c.T).max() < 1e-5 * np.abs(c).max()
+    assert between_bounds(c, [tuple(x) for x in ms.lame], ms.volume_fractions())
+    H.close()
