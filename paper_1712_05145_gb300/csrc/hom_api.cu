@@ -18,6 +18,7 @@
 
 #include "aux.h"
 #include "hierarchy.h"
+#include "zsplit.h"
 #include "hom.h"
 #include "internal.h"
 
@@ -388,7 +389,21 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArg
     za.S = S;
     ia.S = S;
     CKS(fwd_xy<Tf1, T>(c, fa, n));
-    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(za, n, c->stream); }));
+    if (za.mode == Z_GAMMA && za.ncomp_in == 6 && ((size_t)1 << za.tc_log2) * sizeof(cx<T>) < 32) {
+      // deep grid: the fused z tiles would be narrower than a sector; split the z stage into
+      // per-component z FFTs (one "load" per component, all loads of the chunk processed) and
+      // a pointwise contraction
+      ZArgs<T> zf = z_args<T>(c, Z_FWD, 1, 1);
+      zpass_tiling<T>(zf, -1);
+      zf.S = S;
+      ZArgs<T> zi = zf;
+      zi.mode = Z_INV;
+      CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(zf, 6 * n, c->stream); }));
+      CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zgreen<T>(za, n, c->stream); }));
+      CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(zi, 6 * n, c->stream); }));
+    } else {
+      CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(za, n, c->stream); }));
+    }
     CKS(inv_xy<Tf3, T>(c, ia, n));
   }
   return HOM_OK;

@@ -3,6 +3,7 @@
 #include <utility>
 
 #include "ls_common.cuh"
+#include "zsplit.h"
 
 namespace hom {
 
@@ -65,6 +66,58 @@ __device__ __forceinline__ int wave(int j, int n) {
   if ((n & 1) == 0 && 2 * j == n) k = 0;
   return k;
 }
+
+// Pointwise Green contraction of the split z pass: one thread per frequency and load, the six
+// Kelvin components read and written with unit stride along the spectrum's flat index.
+template <typename T>
+__global__ void __launch_bounds__(256) zgreen_kernel(const ZArgs<T> a, int nrhs) {
+  const Geo& g = a.g;
+  const T c1 = (T)(1.0 / (2.0 * a.mu0));
+  const T c2h = (T)((a.lam0 + a.mu0) / (2.0 * a.mu0 * (a.lam0 + 2.0 * a.mu0)));
+  const T scale = (T)a.scale;
+  const long long per = (long long)g.n3 * g.plane_c;   // frequencies of one component
+  const long long nmain = (long long)g.n2 * g.h;
+  const long long total = (long long)nrhs * per;
+  if (a.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(a.prof, (unsigned long long)(total * 12LL * (long long)sizeof(cx<T>)));
+    atomicAdd(a.prof + 1, (unsigned long long)total);
+  }
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const long long lrhs = id / per, q = id - lrhs * per;
+    if (a.st != nullptr && a.st[a.rhs0 + lrhs].active == 0) continue;
+    const int n = (int)(q / g.plane_c);
+    const long long f = q - (long long)n * g.plane_c;
+    int kx, ky;
+    if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
+    else { ky = (int)(f - nmain); kx = g.h; }
+    const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
+    const T x2 = (T)(wave(ky, g.n2) * g.xs2);
+    const T x3 = (T)(wave(n, g.n3) * g.xs3);
+    cx<T>* base = a.S + lrhs * 6 * per + q;
+    cx<T> k[6], tt[6], w1, w2, w3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) k[i] = base[i * per];
+    kelvin_to_tensor<T>(k, tt);
+    tensor_dot_xi<T>(tt, x1, x2, x3, w1, w2, w3);
+    green_from_w<T>(k, w1, w2, w3, x1, x2, x3, c1, c2h, scale);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) base[i * per] = k[i];
+  }
+}
+
+template <typename T>
+cudaError_t launch_zgreen(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
+  if (nrhs < 1) return cudaErrorInvalidValue;
+  const long long total = (long long)nrhs * a.g.n3 * a.g.plane_c;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  count_launch();
+  zgreen_kernel<T><<<(int)blocks, 256, 0, s>>>(a, nrhs);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zgreen<float>(const ZArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_zgreen<double>(const ZArgs<double>&, int, cudaStream_t);
 
 template <typename T, int EPT>
 __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
