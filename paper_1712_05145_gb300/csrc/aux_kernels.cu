@@ -2,7 +2,6 @@
 // between the public Mandel vectors and the internal Kelvin components, layout changes
 // of spectra, and FP64 voxel means of stresses (the averages behind C_eff, Sec. 2).
 #include "aux.h"
-#include "refine.h"
 
 namespace hom {
 
@@ -122,17 +121,6 @@ __global__ void add_difference_kernel(const float* __restrict__ a, const float* 
 cudaError_t launch_add_difference(const float* a, const float* b, double* x, long long n, cudaStream_t s) {
   count_launch();
   add_difference_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, b, x, n);
-  return cudaGetLastError();
-}
-
-// a -= b
-__global__ void sub_inplace_kernel(float* __restrict__ a, const float* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    a[i] -= b[i];
-}
-cudaError_t launch_sub_inplace(float* a, const float* b, long long n, cudaStream_t s) {
-  count_launch();
-  sub_inplace_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,6 @@
 //   BI_P        p = r + beta (p - omega v), or r_hat = r, p = r after a breakdown (rho' = 0 or
 //               omega = 0), in which case BI_X has already set rho = <r, r>.
 #include "ls_common.cuh"
-#include "refine.h"
 
 namespace hom {
 
@@ -139,46 +138,6 @@ cudaError_t launch_bicg(int step, const BicgArgs<Tf>& a, int nrhs, int nblk, cud
     case BI_P: bicg_kernel<Tf, BI_P><<<grid, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-// Restart residual of the FP32 refinement after a projection of x: r -= eta, then its norms.
-__global__ void __launch_bounds__(256) restart_residual_kernel(float* __restrict__ r, const float* __restrict__ eta,
-                                                               double c0h, double c0d, long long M, RhsState* st,
-                                                               double* part, int pstride, unsigned* cnt) {
-  __shared__ double sh[64 + 2];
-  __shared__ int flag;
-  const int rhs = blockIdx.y;
-  if (st[rhs].active == 0) return;
-  const long long per = 6LL * M, off = (long long)rhs * per;
-  float q0 = 0.0f, q1 = 0.0f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per; i += (long long)gridDim.x * blockDim.x) {
-    const float v = r[off + i] - eta[off + i];
-    r[off + i] = v;
-    const float w = (i < M) ? (float)c0h : (float)c0d;
-    q0 += w * v * v;
-    q1 += v * v;
-  }
-  double v[2] = {(double)q0, (double)q1};
-  block_sum_f64<2>(v, sh);
-  if (publish_and_collect<2>(v, part + (long long)rhs * 2 * pstride, cnt + rhs, gridDim.x, blockIdx.x, sh, &flag)) {
-    if (threadIdx.x == 0) {
-      RhsState& s = st[rhs];
-      const double invM = 1.0 / (double)M;
-      s.rho = v[0] * invM;
-      s.res_true = (s.b2 > 0.0) ? sqrt(v[1] * invM / s.b2) : 0.0;
-      s.res = s.res_true;
-      s.restart = 1;
-      if (!isfinite(s.res_true)) { s.status = 2; s.active = 0; }
-    }
-  }
-}
-
-cudaError_t launch_restart_residual(float* r, const float* eta, double c0h, double c0d, long long M, RhsState* st,
-                                    double* part, int pstride, unsigned* cnt, int nrhs, int nblk, cudaStream_t s) {
-  if (nblk < 1 || nblk > pstride || nrhs < 1) return cudaErrorInvalidValue;
-  count_launch();
-  restart_residual_kernel<<<dim3(nblk, nrhs), 256, 0, s>>>(r, eta, c0h, c0d, M, st, part, pstride, cnt);
   return cudaGetLastError();
 }
 

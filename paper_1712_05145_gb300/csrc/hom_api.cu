@@ -18,7 +18,6 @@
 
 #include "aux.h"
 #include "hierarchy.h"
-#include "refine.h"
 #include "zsplit.h"
 #include "hom.h"
 #include "internal.h"
@@ -464,34 +463,6 @@ hom_status project_compatible_fp32(hom_ctx* c, int n, double* x64, float* x32, f
   return HOM_OK;
 }
 
-// After the loose first FP32 sweep: removes the incompatible part i of x in FP32 and moves the CG
-// residual r (the FP32 recursion's b - Gamma0 * (C : (x + E))) to that of the projected x,
-// r <- r + Gamma0 * (C : i), with the FP32 operator applied to the small field i only.  It
-// stands in for an FP64 residual sweep here; the literal FP64 check at the end of a later sweep
-// still decides convergence.  s1 and s2 are FP32 scratch of n loads (the correction d and the
-// direction p, both free at a restart); s1 is returned zeroed.
-hom_status restart_after_projection_fp32(hom_ctx* c, int n, double* x64, float* r, float* s1, float* s2,
-                                         const std::vector<int>* act) {
-  const long long cnt = (long long)n * 6 * c->g.M;
-  CKS(project_compatible_fp32(c, n, x64, s1, s2, act));   // s1 = x32, s2 = P(x32), x64 += s2 - s1
-  CK(launch_sub_inplace(s1, s2, cnt, c->stream));         // s1 = i = x32 - P(x32)
-  auto fa = fwd_args<float, float>(c, FWD_STRESS, 6, 6);
-  fa.in = s1;
-  fa.st = c->d_st;
-  auto za = z_args<float>(c, Z_GAMMA, 6, 6);
-  za.st = c->d_st;
-  auto ia = inv_args<float, float>(c, INV_STORE, FIN_NONE, 6, 6, 6);
-  ia.out = s2;                                             // s2 = eta(i) = -Gamma0 * (C : i)
-  ia.st = c->d_st;
-  CKS((ls_pass<float, float, float>(c, n, fa, za, ia, act)));
-  const int pstride = (int)ncta_max(c);
-  const int nblk = std::max(1, std::min(pstride, std::max(64, (152 * 8) / n)));
-  CK(launch_restart_residual(r, s2, 3.0 * c->lam0 + 2.0 * c->mu0, 2.0 * c->mu0, c->g.M, c->d_st, part_fwd(c),
-                             pstride, cnt_fwd(c), n, nblk, c->stream));
-  CK(cudaMemsetAsync(s1, 0, sizeof(float) * (size_t)cnt, c->stream));
-  return HOM_OK;
-}
-
 // FP64 residual sweep r = b - A x, evaluated as b - Gamma0 * (C : (x + E)) (Eq. cg_form with
 // A = Gamma0 * C on compatible fields): equal to the literal residual on compatible x, and
 // itself exactly compatible, so CG restarts inside the subspace where A is self-adjoint in the
@@ -872,24 +843,13 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
         for (int i = 0; i < n; ++i)
           if (act[i] && (refine[i] > 0 || st[i].tol <= tol)) loose = false;
         if (loose) {
-          CKS(restart_after_projection_fp32(c, n, x64, reinterpret_cast<float*>(r), reinterpret_cast<float*>(d),
-                                            reinterpret_cast<float*>(p), &act));
-          // the FP32 estimate may not certify convergence: a load it puts below tol (an easy
-          // problem, solved in the loose sweep) gets the FP64 projection and residual instead
-          CKS(read_states(c, n, st));
-          bool below = false;
-          for (int i = 0; i < n; ++i) below = below || (act[i] && st[i].res_true < tol);
-          if (below) {
-            CKS(project_compatible(c, n, x64, &act));
-            CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
-          }
+          CKS(project_compatible_fp32(c, n, x64, reinterpret_cast<float*>(d), reinterpret_cast<float*>(r), &act));
+          CK(cudaMemsetAsync(d, 0, fb, c->stream));   // d was scratch; the next sweep starts from 0
         } else {
           CKS(project_compatible(c, n, x64, &act));
-          CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
         }
-      } else {
-        CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       }
+      CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       CKS(read_states(c, n, st));
       bool again = false;
       for (int i = 0; i < n; ++i) {
