@@ -12,6 +12,50 @@
 
 namespace hom {
 
+// Double-float number: the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about
+// 48 significant bits.  The FP32 mode's FP64 passes (residuals, literal checks, projections) run
+// in it: on this GPU the FP64 pipe executes a small fraction of the FP32 rate, and these passes
+// need about 1e-12 relative accuracy, not 53 bits.  Sums use Knuth's TwoSum and Dekker's
+// FastTwoSum, products an FMA-exact product (the standard error-free transformations); the
+// division goes through double and is used once per frequency only.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr df64(float f) : hi(f), lo(0.0f) {}
+  __host__ __device__ constexpr df64(int i) : df64((double)i) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return df64(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return df64(s, b - (s - a));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const df64 s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) { return df64((double)a / (double)b); }
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
+
 template <typename T>
 struct alignas(2 * sizeof(T)) cx {
   T re, im;
@@ -33,6 +77,10 @@ __device__ __forceinline__ cx<float> ldg_cx(const cx<float>* p) {
 __device__ __forceinline__ cx<double> ldg_cx(const cx<double>* p) {
   double2 f = __ldg(reinterpret_cast<const double2*>(p));
   return mk<double>(f.x, f.y);
+}
+__device__ __forceinline__ cx<df64> ldg_cx(const cx<df64>* p) {
+  float4 f = __ldg(reinterpret_cast<const float4*>(p));
+  return mk<df64>(df64(f.x, f.y), df64(f.z, f.w));
 }
 // multiply by +i (s = +1) or -i (s = -1)
 template <typename T, int S> __device__ __forceinline__ cx<T> mul_i(cx<T> a) {

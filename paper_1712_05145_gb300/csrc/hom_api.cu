@@ -81,6 +81,8 @@ struct hom_ctx {
   double* d_mat64 = nullptr;
   float* d_mat32 = nullptr;
   cx<double>* d_tw64 = nullptr;
+  df64* d_mat_df = nullptr;     // the FP64 tables as double-float (FP32 mode's FP64 passes)
+  cx<df64>* d_tw_df = nullptr;
   cx<float>* d_tw32 = nullptr;
   long long tw_off[4] = {0, 0, 0, 0};
   void* d_S = nullptr;  // compute-precision spectrum, `chunk` loads (>= 9 component planes)
@@ -219,9 +221,11 @@ unsigned* cnt_inv(hom_ctx* c) { return c->d_cnt + c->cap; }
 template <typename T> const T* mat_ptr(hom_ctx* c);
 template <> const float* mat_ptr<float>(hom_ctx* c) { return c->d_mat32; }
 template <> const double* mat_ptr<double>(hom_ctx* c) { return c->d_mat64; }
+template <> const df64* mat_ptr<df64>(hom_ctx* c) { return c->d_mat_df; }
 template <typename T> const cx<T>* tw(hom_ctx* c, int i);
 template <> const cx<float>* tw<float>(hom_ctx* c, int i) { return c->d_tw32 + c->tw_off[i]; }
 template <> const cx<double>* tw<double>(hom_ctx* c, int i) { return c->d_tw64 + c->tw_off[i]; }
+template <> const cx<df64>* tw<df64>(hom_ctx* c, int i) { return c->d_tw_df + c->tw_off[i]; }
 
 template <typename Tf, typename T>
 FwdArgs<Tf, T> fwd_args(hom_ctx* c, int mode, int ncomp, int in_ncomp) {
@@ -291,6 +295,9 @@ template <> cx<double>* spec<double>(hom_ctx* c, int* chunk) {
   }
   *chunk = c->chunk;
   return reinterpret_cast<cx<double>*>(c->d_S);
+}
+template <> cx<df64>* spec<df64>(hom_ctx* c, int* chunk) {   // same bytes per value as double
+  return reinterpret_cast<cx<df64>*>(spec<double>(c, chunk));
 }
 
 cudaEvent_t pool_event(hom_ctx* c) {
@@ -429,17 +436,23 @@ size_t tbytes(const hom_ctx* c, int nf, int ncomp) {
 // FP32 corrections carry rounding noise that is not compatible; left in x, the compatible-
 // subspace residual below would turn it into a compatible error scaled by the stiffness
 // contrast.  Projected, x differs from the solution only by compatible errors the residual sees.
-hom_status project_compatible(hom_ctx* c, int n, double* x64, const std::vector<int>* act) {
-  auto fa = fwd_args<double, double>(c, FWD_C0, 6, 6);
+template <typename TC>
+hom_status project_compatible_t(hom_ctx* c, int n, double* x64, const std::vector<int>* act) {
+  auto fa = fwd_args<double, TC>(c, FWD_C0, 6, 6);
   fa.in = x64;
   fa.st = c->d_st;
-  auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+  auto za = z_args<TC>(c, Z_GAMMA, 6, 6);
   za.st = c->d_st;
-  auto ia = inv_args<double, double>(c, INV_STORE, FIN_NONE, 6, 6, 6);
+  auto ia = inv_args<double, TC>(c, INV_STORE, FIN_NONE, 6, 6, 6);
   ia.out = x64;
-  ia.out_scale = -1.0;
+  ia.out_scale = (TC)(-1.0);
   ia.st = c->d_st;
-  return ls_pass<double, double, double>(c, n, fa, za, ia, act);
+  return ls_pass<double, double, TC>(c, n, fa, za, ia, act);
+}
+// FP64 mode computes in double; the FP32 mode's FP64 passes compute in double-float, which
+// keeps about 48 bits (far more than these checks need) at a fraction of the FP64 pipe's cost.
+hom_status project_compatible(hom_ctx* c, int n, double* x64, const std::vector<int>* act) {
+  return c->fp32 ? project_compatible_t<df64>(c, n, x64, act) : project_compatible_t<double>(c, n, x64, act);
 }
 
 // The same projection computed in FP32: x32 = fp32(x), p32 = Gamma0 * (C0 : x32) in FP32, and
@@ -467,20 +480,26 @@ hom_status project_compatible_fp32(hom_ctx* c, int n, double* x64, float* x32, f
 // A = Gamma0 * C on compatible fields): equal to the literal residual on compatible x, and
 // itself exactly compatible, so CG restarts inside the subspace where A is self-adjoint in the
 // C0 product.  x and b are FP64; r is written in the iteration precision Tf.
-template <typename Tf>
-hom_status residual_sweep(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
+template <typename Tf, typename TC>
+hom_status residual_sweep_t(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
                           int fin, const std::vector<int>* act) {
-  auto fa = fwd_args<double, double>(c, FWD_STRESS, 6, 6);
+  auto fa = fwd_args<double, TC>(c, FWD_STRESS, 6, 6);
   fa.in = x64;
   fa.E = dE;
   fa.st = c->d_st;
-  auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+  auto za = z_args<TC>(c, Z_GAMMA, 6, 6);
   za.st = c->d_st;
-  auto ia = inv_args<Tf, double>(c, INV_STORE, fin, 6, 6, 6);
+  auto ia = inv_args<Tf, TC>(c, INV_STORE, fin, 6, 6, 6);
   ia.out = r;
   ia.b = b64;
   ia.st = c->d_st;
-  return ls_pass<double, Tf, double>(c, n, fa, za, ia, act);
+  return ls_pass<double, Tf, TC>(c, n, fa, za, ia, act);
+}
+template <typename Tf>
+hom_status residual_sweep(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
+                          int fin, const std::vector<int>* act) {
+  return c->fp32 ? residual_sweep_t<Tf, df64>(c, n, dE, b64, x64, r, fin, act)
+                 : residual_sweep_t<Tf, double>(c, n, dE, b64, x64, r, fin, act);
 }
 
 // out = A in = Gamma0 * (C : in) for compatible in (Eq. cg_form), one LS pass with the sign of
@@ -610,21 +629,27 @@ hom_status bicgstab_sweep(hom_ctx* c, int n, Tf* x, Tf* r, Tf* p, std::vector<Rh
 // one LS pass, tau = (C - C0) : (x + E), r = -Gamma0 * tau + b - x (for order 0, b is the E term
 // inside tau).  Unlike residual_sweep it sees an incompatible part of x, so a value below tol
 // certifies the solution without a projection.
-template <typename Tf>
-hom_status literal_residual(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
+template <typename Tf, typename TC>
+hom_status literal_residual_t(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
                             const std::vector<int>* act) {
-  auto fa = fwd_args<double, double>(c, FWD_TAU, 6, 6);
+  auto fa = fwd_args<double, TC>(c, FWD_TAU, 6, 6);
   fa.in = x64;
   fa.E = dE;
   fa.st = c->d_st;
-  auto za = z_args<double>(c, Z_GAMMA, 6, 6);
+  auto za = z_args<TC>(c, Z_GAMMA, 6, 6);
   za.st = c->d_st;
-  auto ia = inv_args<Tf, double>(c, INV_STORE, FIN_RESID, 6, 6, 6);
+  auto ia = inv_args<Tf, TC>(c, INV_STORE, FIN_RESID, 6, 6, 6);
   ia.out = r;
   ia.b = b64;
   ia.xsub = x64;
   ia.st = c->d_st;
-  return ls_pass<double, Tf, double>(c, n, fa, za, ia, act);
+  return ls_pass<double, Tf, TC>(c, n, fa, za, ia, act);
+}
+template <typename Tf>
+hom_status literal_residual(hom_ctx* c, int n, const double* dE, const double* b64, const double* x64, Tf* r,
+                            const std::vector<int>* act) {
+  return c->fp32 ? literal_residual_t<Tf, df64>(c, n, dE, b64, x64, r, act)
+                 : literal_residual_t<Tf, double>(c, n, dE, b64, x64, r, act);
 }
 
 // Solves A x = b (Eq. cg_form) for n loads; b = -Gamma0 * (C : E) for Kelvin loads dE (order 0,
@@ -1435,6 +1460,10 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if ((s = dalloc(c, (void**)&c->d_mat32, sizeof(float) * 4 * 256)) != HOM_OK) return bail(s);
   cudaMemcpy(c->d_mat64, m64.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_mat32, m32.data(), sizeof(float) * 4 * 256, cudaMemcpyHostToDevice);
+  std::vector<df64> mdf(4 * 256, df64(0.0f, 0.0f));
+  for (int i = 0; i < 4 * 256; ++i) mdf[i] = df64(m64[i]);
+  if ((s = dalloc(c, (void**)&c->d_mat_df, sizeof(df64) * 4 * 256)) != HOM_OK) return bail(s);
+  cudaMemcpy(c->d_mat_df, mdf.data(), sizeof(df64) * 4 * 256, cudaMemcpyHostToDevice);
 
   // twiddle tables exp(-2 pi i t / L) for L = h, n1, n2, n3 (host libm, FP64)
   std::vector<cx<double>> t64;
@@ -1452,6 +1481,13 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if ((s = dalloc(c, (void**)&c->d_tw32, sizeof(cx<float>) * t32.size())) != HOM_OK) return bail(s);
   cudaMemcpy(c->d_tw64, t64.data(), sizeof(cx<double>) * t64.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_tw32, t32.data(), sizeof(cx<float>) * t32.size(), cudaMemcpyHostToDevice);
+  std::vector<cx<df64>> tdf(t64.size());
+  for (size_t i = 0; i < t64.size(); ++i) {
+    tdf[i].re = df64(t64[i].re);
+    tdf[i].im = df64(t64[i].im);
+  }
+  if ((s = dalloc(c, (void**)&c->d_tw_df, sizeof(cx<df64>) * tdf.size())) != HOM_OK) return bail(s);
+  cudaMemcpy(c->d_tw_df, tdf.data(), sizeof(cx<df64>) * tdf.size(), cudaMemcpyHostToDevice);
 
   // spectrum scratch
   const size_t elem = c->fp32 ? sizeof(cx<float>) : sizeof(cx<double>);

@@ -31,6 +31,9 @@ template <> struct PlaneCfg<float> {   // 64 registers: 2 CTAs per SM
 template <> struct PlaneCfg<double> {
   static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
 };
+template <> struct PlaneCfg<df64> {
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
+};
 // threads of a plane CTA: every element of the n2 x h plane has a slot, whole warps, >= 128
 template <typename T>
 inline int plane_threads(const Geo& g) {

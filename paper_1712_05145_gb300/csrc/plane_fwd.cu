@@ -290,6 +290,7 @@ void zpass_tiling(ZArgs<T>& a, int force_lg) {
 }
 template void zpass_tiling<float>(ZArgs<float>&, int);
 template void zpass_tiling<double>(ZArgs<double>&, int);
+template void zpass_tiling<df64>(ZArgs<df64>&, int);
 
 template <typename Tf, typename T>
 cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) {
@@ -309,5 +310,6 @@ cudaError_t launch_plane_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
 
 template cudaError_t launch_plane_fwd<float, float>(const FwdArgs<float, float>&, int, cudaStream_t);
 template cudaError_t launch_plane_fwd<double, double>(const FwdArgs<double, double>&, int, cudaStream_t);
+template cudaError_t launch_plane_fwd<double, df64>(const FwdArgs<double, df64>&, int, cudaStream_t);
 
 }  // namespace hom

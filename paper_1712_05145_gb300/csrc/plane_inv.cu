@@ -208,5 +208,7 @@ cudaError_t launch_plane_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s) 
 template cudaError_t launch_plane_inv<float, float>(const InvArgs<float, float>&, int, cudaStream_t);
 template cudaError_t launch_plane_inv<double, double>(const InvArgs<double, double>&, int, cudaStream_t);
 template cudaError_t launch_plane_inv<float, double>(const InvArgs<float, double>&, int, cudaStream_t);
+template cudaError_t launch_plane_inv<float, df64>(const InvArgs<float, df64>&, int, cudaStream_t);
+template cudaError_t launch_plane_inv<double, df64>(const InvArgs<double, df64>&, int, cudaStream_t);
 
 }  // namespace hom

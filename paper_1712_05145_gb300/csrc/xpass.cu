@@ -297,5 +297,8 @@ template cudaError_t launch_xpass_fwd<double, double>(const FwdArgs<double, doub
 template cudaError_t launch_xpass_inv<float, float>(const InvArgs<float, float>&, int, cudaStream_t);
 template cudaError_t launch_xpass_inv<double, double>(const InvArgs<double, double>&, int, cudaStream_t);
 template cudaError_t launch_xpass_inv<float, double>(const InvArgs<float, double>&, int, cudaStream_t);
+template cudaError_t launch_xpass_fwd<double, df64>(const FwdArgs<double, df64>&, int, cudaStream_t);
+template cudaError_t launch_xpass_inv<float, df64>(const InvArgs<float, df64>&, int, cudaStream_t);
+template cudaError_t launch_xpass_inv<double, df64>(const InvArgs<double, df64>&, int, cudaStream_t);
 
 }  // namespace hom

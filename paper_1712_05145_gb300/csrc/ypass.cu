@@ -92,5 +92,7 @@ template cudaError_t launch_ypass<float>(const cx<float>*, cx<float>*, const Geo
                                          unsigned long long*, const RhsState*, int, cudaStream_t);
 template cudaError_t launch_ypass<double>(const cx<double>*, cx<double>*, const Geo&, int, int, int, int,
                                           unsigned long long*, const RhsState*, int, cudaStream_t);
+template cudaError_t launch_ypass<df64>(const cx<df64>*, cx<df64>*, const Geo&, int, int, int, int,
+                                        unsigned long long*, const RhsState*, int, cudaStream_t);
 
 }  // namespace hom

@@ -118,6 +118,7 @@ cudaError_t launch_zgreen(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
 }
 template cudaError_t launch_zgreen<float>(const ZArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_zgreen<double>(const ZArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_zgreen<df64>(const ZArgs<df64>&, int, cudaStream_t);
 
 template <typename T, int EPT>
 __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
@@ -269,8 +270,10 @@ int zpass_ctas_per_sm(int threads, size_t smem) {
 }
 template int zpass_ctas_per_sm<float>(int, size_t);
 template int zpass_ctas_per_sm<double>(int, size_t);
+template int zpass_ctas_per_sm<df64>(int, size_t);
 
 template cudaError_t launch_zpass<float>(const ZArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_zpass<double>(const ZArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_zpass<df64>(const ZArgs<df64>&, int, cudaStream_t);
 
 }  // namespace hom
