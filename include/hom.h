@@ -177,7 +177,8 @@ HOM_API hom_status hom_fft_inverse(hom_t h, int32_t nfield, const double* fhat, 
 HOM_API hom_status hom_green_apply(hom_t h, int32_t nrhs, const double* tau_hat, double* eta_hat);
 
 /* Per-kernel accounting for performance measurement (off by default).
- * Kernel kinds of the Lippmann-Schwinger step, with FFTs in FP32 (0..2) or FP64 (3..5): */
+ * Kernel kinds of the Lippmann-Schwinger step, with FFTs in FP32 (0..2) or at FP64 accuracy (3..5:
+ * double in HOM_FP64, double-float in the FP64-accurate passes of HOM_FP32_REFINE): */
 enum {
   HOM_KERNEL_PLANE_FWD = 0, HOM_KERNEL_ZPASS = 1, HOM_KERNEL_PLANE_INV = 2,
   HOM_KERNEL_PLANE_FWD_F64 = 3, HOM_KERNEL_ZPASS_F64 = 4, HOM_KERNEL_PLANE_INV_F64 = 5,

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import closed_forms
 from oracle.lippmann_schwinger import Problem
-from oracle.tensors import tensor_to_mandel, unit_mandel_load
+from oracle.tensors import mandel_to_tensor, tensor_to_mandel, unit_mandel_load
 from paper_1712_05145_gb300 import synthetic
 from tests.helpers import TOL, TOL_EFF, random_phase, rel_err
 
@@ -177,3 +177,19 @@ def test_autotuned_launch_shape_gives_identical_results(precision):
         H.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2] == out[1][2]
+
+
+def test_fp32_mode_residual_certified_at_1e10():
+    """The FP32 mode's FP64 passes (double-float arithmetic) certify a residual of 1e-10: the
+    oracle recomputes the literal residual of the GPU solution and agrees with the reported one."""
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.random_spheres((24, 24, 24), seed=5, inclusion_e=100.0)
+    pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, max_refine=12)
+    info = H.solve(0, 1e-10, loads=np.eye(6)[[0, 3]])
+    assert all(i["status"] == 0 for i in info), info
+    for k, a in enumerate((0, 3)):
+        res = pb.residual(mandel_to_tensor(H.field(0, k)), pb.rhs(unit_mandel_load(a)))
+        assert res < 1e-10, (a, res)
+        assert abs(res - info[k]["rel_residual_fp64"]) < 0.05 * res + 1e-13, (res, info[k])
+    H.close()
