@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--rhs-chunk", type=int, default=0,
                     help="loads transformed per launch (0: as many as fit the spectrum budget)")
     ap.add_argument("--spectrum-budget-mb", type=int, default=1024, help="spectrum scratch budget")
+    ap.add_argument("--check-every", type=int, default=8,
+                    help="iterations between host reads of the per-load solver state")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed launch-shape rules instead of timing the candidates before the first solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -230,7 +232,8 @@ def main():
     torch.cuda.set_stream(stream)
     H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, scheme=hom.HOM_CG, stream=stream.cuda_stream,
                            rhs_chunk=args.rhs_chunk, spectrum_budget_bytes=args.spectrum_budget_mb << 20,
-                           autotune=0 if (args.no_autotune or args.rhs_chunk) else 1)
+                           autotune=0 if (args.no_autotune or args.rhs_chunk) else 1,
+                           check_every=args.check_every)
 
     def step():
         info = H.solve(0, TOL)
@@ -329,6 +332,7 @@ def main():
         "config": {"workload": WORKLOAD, "grid": [n, n, n], "loads": 6, "tol": TOL, "seed": SEED,
                    "rhs_chunk": args.rhs_chunk, "spectrum_budget_mb": args.spectrum_budget_mb,
                    "loads_per_launch": launch_cfg[0], "ztile_log2": launch_cfg[1],
+                   "check_every": args.check_every,
                    "l2": "inputs larger than L2 (x, r, p fields 302 MB each)", "parallelism": "replicas"},
         "solves_per_s": world * args.steps / (total_ms / 1e3),
         "p50_ms": float(np.percentile(step_ms, 50)),
