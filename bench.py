@@ -132,9 +132,8 @@ def ncu_traffic(kernel):
     return ent.get("dram_bytes_per_launch_full")
 
 
-def cpu_baseline():
-    """The oracle as it stands: two A-applications (two CG iterations' LS steps) of one load on the
-    same 128^3 microstructure, single-threaded numpy on this host (about 10-15 s)."""
+def _oracle_sample(load):
+    """Child process: two oracle A-applications of unit load `load` on the 128^3 RVE, one thread."""
     code = r"""
 import os, sys, time, json
 sys.path.insert(0, %r)
@@ -144,19 +143,43 @@ from oracle.lippmann_schwinger import Problem
 from oracle.tensors import unit_mandel_load
 ms = synthetic.random_spheres((%d,)*3, seed=%d)
 pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
-b = pb.rhs(unit_mandel_load(0))
+b = pb.rhs(unit_mandel_load(%d))
 t = time.perf_counter(); q = pb.apply_A(b); q = pb.apply_A(q); dt = time.perf_counter() - t
 print(json.dumps({"seconds": dt, "voxel_iters": 2 * ms.phase.size}))
-""" % (ROOT, GRID, SEED)
+""" % (ROOT, GRID, SEED, load)
     envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                            text=True, env=envv)
+
+
+def cpu_baseline():
+    """The oracle as it stands: two A-applications (two CG iterations' LS steps) of one load on the
+    same 128^3 microstructure, single-threaded numpy on this host (about 10-15 s).  Beside it, the
+    same sample for the 6 loads at once, one process per load on the host's cores: the oracle's
+    throughput when the independent loads run in parallel."""
     try:
-        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv, timeout=900)
-        r = json.loads(out.stdout.strip().splitlines()[-1])
-        return {"value": r["voxel_iters"] / r["seconds"], "unit": "voxel-iters/s", "cores": 1, "kind": "oracle",
-                "sample": "two oracle A-applications (LS steps) of load E=e11 on the same 128^3 RVE, "
-                          "numpy FP64 single-threaded, %.1f s" % r["seconds"]}
+        p = _oracle_sample(0)
+        out, _ = p.communicate(timeout=900)
+        r = json.loads(out.strip().splitlines()[-1])
+        res = {"value": r["voxel_iters"] / r["seconds"], "unit": "voxel-iters/s", "cores": 1, "kind": "oracle",
+               "sample": "two oracle A-applications (LS steps) of load E=e11 on the same 128^3 RVE, "
+                         "numpy FP64 single-threaded, %.1f s" % r["seconds"]}
     except Exception as e:  # report, never fail the bench on the baseline leg
         return {"value": None, "unit": "voxel-iters/s", "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
+    try:
+        nproc = min(6, os.cpu_count() or 1)
+        t0 = time.perf_counter()
+        procs = [_oracle_sample(a) for a in range(nproc)]
+        vi = 0
+        for q in procs:
+            o, _ = q.communicate(timeout=900)
+            vi += json.loads(o.strip().splitlines()[-1])["voxel_iters"]
+        wall = time.perf_counter() - t0
+        res["all_cores"] = {"value": vi / wall, "unit": "voxel-iters/s", "cores": nproc,
+                            "sample": "the same sample for %d loads, one process per load, %.1f s wall" % (nproc, wall)}
+    except Exception as e:
+        res["all_cores"] = {"value": None, "sample": "failed: %s" % e}
+    return res
 
 
 def reference_arm(args):
