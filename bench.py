@@ -103,7 +103,7 @@ class ClockSampler:
 # it includes); the committed DRAM counters of a kind are used only while these are unchanged
 KERNEL_SOURCES = {
     "plane_fwd": ["plane_fwd.cu"], "plane_fwd_f64": ["plane_fwd.cu"],
-    "zpass": ["zpass.cu"], "zpass_f64": ["zpass.cu"],
+    "zpass": ["zpass.cu", "spectral.cuh"], "zpass_f64": ["zpass.cu", "spectral.cuh"],
     "plane_inv": ["plane_inv.cu"], "plane_inv_f64": ["plane_inv.cu"],
     "ypass": ["ypass.cu"], "ypass_f64": ["ypass.cu"],
 }
@@ -300,6 +300,8 @@ def main():
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     worst = [i["rel_residual_fp64"] for i in info]
+    # untimed diagnostic: sqrt(<|div sigma|^2>) / |<sigma>| of each load's solution
+    eq_err = [float(v) for v in H.equilibrium_error()]
 
     total_ms, job_vi = replicas.aggregate(total_ms, float(M) * iters, device="cuda")
     value = job_vi / (total_ms / 1e3)
@@ -363,8 +365,10 @@ def main():
         "cg_iterations_per_step": per_step_iters,
         "fp64_refinements_per_load": per_step_refine[-1],
         "per_load": [{"iterations": i["iterations"], "rel_residual": i["rel_residual"],
-                      "rel_residual_fp64": i["rel_residual_fp64"]} for i in info],
+                      "rel_residual_fp64": i["rel_residual_fp64"], "equilibrium_error": e}
+                     for i, e in zip(info, eq_err)],
         "rel_residual_fp64_max": max(worst),
+        "equilibrium_error_max": max(eq_err),
         "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "bytes_per_launch": dom["bytes"] / max(1, dom["launches"]),

@@ -155,6 +155,23 @@ HOM_API hom_status hom_effective(hom_t h, int32_t order, double* out);
 HOM_API hom_status hom_get_field(hom_t h, int32_t order, int32_t load, int32_t kind, double* dst,
                                  int32_t dst_on_device);
 
+/* Equilibrium error of stress fields sigma = C : (E + eps) (Sec. 2, Eq. Hookes_law): how far
+ * sigma is from the balance of momentum div sigma = 0 (Eq. eq_of_motion), in the spectral form
+ * of Moulinec and Suquet (the paper's reference for the Basic Scheme),
+ *   out[l] = sqrt(< |div sigma|^2 >) / |<sigma>|,   (div sigma)_hat(xi) = i xi . sigma_hat(xi),
+ * with the discrete wave vectors of the Green operator (Nyquist components 0), <.> the voxel
+ * mean and |.| the Frobenius norm.  Where the mean vanishes up to rounding (|<sigma>| <=
+ * 1e-12 sqrt(<|sigma|^2>), e.g. a zero load), out[l] = sqrt(< |div sigma|^2 >).  A
+ * solution of the discrete Lippmann-Schwinger equation has out = 0 up to its residual.
+ *   eps != NULL: device double [nrhs][6][N3][N2][N1] Mandel strain fluctuations (nrhs <= 64),
+ *                E host double [nrhs][6] Mandel (NULL = zero);
+ *   eps == NULL: the handle's order-0 solutions and their loads (nrhs = their count, E unused;
+ *                HOM_ERR_ORDER if order 0 has not been solved).
+ * out: host double [nrhs].  Computed at FP64 accuracy (double, or double-float transforms in
+ * HOM_FP32_REFINE).  Not part of a solve; costs one forward transform per field. */
+HOM_API hom_status hom_equilibrium_error(hom_t h, int32_t nrhs, const double* eps, const double* E,
+                                         double* out);
+
 /* One Lippmann-Schwinger step on caller device buffers (Sec. 2, Algorithm 1 loop body):
  *   eps_out = -Gamma0 * [(C - C0) : (eps_in + E)]
  * eps_in, eps_out: device double [nrhs][6][N3][N2][N1] Mandel (eps_in NULL = zero field);

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "aux.h"
+#include "equilibrium.h"
 #include "hierarchy.h"
 #include "zsplit.h"
 #include "hom.h"
@@ -453,6 +454,33 @@ hom_status project_compatible_t(hom_ctx* c, int n, double* x64, const std::vecto
 // keeps about 48 bits (far more than these checks need) at a fraction of the FP64 pipe's cost.
 hom_status project_compatible(hom_ctx* c, int n, double* x64, const std::vector<int>* act) {
   return c->fp32 ? project_compatible_t<df64>(c, n, x64, act) : project_compatible_t<double>(c, n, x64, act);
+}
+
+// Equilibrium error of sigma = C : (epsK + E) for n loads (Kelvin FP64 fields, E in c->d_E): the
+// stress spectrum (plane pass in FWD_STRESS mode, then the z FFT one component at a time), its
+// weighted sum of |xi . sigma_hat|^2 per CTA, and one finishing kernel for all loads.  T is the
+// transform type (double, or double-float in the FP32 mode).  out: device double [n].
+template <typename T>
+hom_status equilibrium_t(hom_ctx* c, int n, const double* epsK, double* d_part, double* d_s0, double* d_out) {
+  const int nblk = equilibrium_blocks(c->g);
+  int chunk;
+  cx<T>* S = spec<T>(c, &chunk);
+  for (int r0 = 0; r0 < n; r0 += chunk) {
+    const int m = std::min(chunk, n - r0);
+    auto fa = fwd_args<double, T>(c, FWD_STRESS, 6, 6);
+    fa.in = epsK;
+    fa.E = c->d_E;
+    fa.rhs0 = r0;
+    fa.S = S;
+    CKS((fwd_xy<double, T>(c, fa, m)));
+    ZArgs<T> zf = z_args<T>(c, Z_FWD, 1, 1);
+    zpass_tiling<T>(zf, -1);
+    zf.S = S;
+    CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zpass<T>(zf, 6 * m, c->stream); }));
+    CK(launch_equilibrium_partials<T>(S, c->g, m, r0, d_part, d_s0, nblk, c->stream));
+  }
+  CK(launch_equilibrium_finish(d_part, d_s0, n, nblk, c->g.M, d_out, c->stream));
+  return HOM_OK;
 }
 
 // The same projection computed in FP32: x32 = fp32(x), p32 = Gamma0 * (C0 : x32) in FP32, and
@@ -1565,6 +1593,40 @@ HOM_API hom_status hom_get_field(hom_t c, int32_t order, int32_t load, int32_t k
   hom_status s = export_field(c, order, load, kind, d);
   if (s != HOM_OK) return s;
   if (!dst_on_device) CK(cudaMemcpyAsync(dst, d, nbytes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+HOM_API hom_status hom_equilibrium_error(hom_t c, int32_t nrhs, const double* eps, const double* E, double* out) {
+  if (!c || !out) return HOM_ERR_ARG;
+  const OrderData& o = c->ord[0];
+  if (!eps) {
+    if (!o.eps || o.eff.empty()) return fail(c, HOM_ERR_ORDER, "order 0 has not been solved");
+    if (nrhs != o.nloads) return fail(c, HOM_ERR_ARG, "nrhs must equal the %d solved order-0 loads", o.nloads);
+  } else if (nrhs < 1 || nrhs > 64) {
+    return fail(c, HOM_ERR_ARG, "1 to 64 fields per call");
+  }
+  CKS(ensure_cap(c, nrhs));
+  std::vector<double> ek(6 * nrhs, 0.0);
+  if (!eps) ek = o.loadsK;
+  else if (E) for (int i = 0; i < nrhs; ++i) mandel_to_kelvin6(E + 6 * i, &ek[6 * i]);
+  CK(cudaMemcpyAsync(c->d_E, ek.data(), sizeof(double) * 6 * nrhs, cudaMemcpyHostToDevice, c->stream));
+  const double* epsK = reinterpret_cast<const double*>(o.eps);
+  if (eps) {
+    void* vin;
+    CKS(work(c, 0, std::max(tbytes<double>(c, nrhs, 6), c->work_bytes[0]), &vin));
+    CK(launch_mandel_to_kelvin<double>(eps, (double*)vin, c->g.M, nrhs, c->stream));
+    epsK = (const double*)vin;
+  }
+  const int nblk = equilibrium_blocks(c->g);
+  void* vred;
+  CKS(work(c, 1, std::max(sizeof(double) * (size_t)nrhs * (2 * nblk + 7), c->work_bytes[1]), &vred));
+  double* d_part = (double*)vred;
+  double* d_s0 = d_part + (size_t)nrhs * 2 * nblk;
+  double* d_out = d_s0 + (size_t)nrhs * 6;
+  CKS(c->fp32 ? equilibrium_t<df64>(c, nrhs, epsK, d_part, d_s0, d_out)
+              : equilibrium_t<double>(c, nrhs, epsK, d_part, d_s0, d_out));
+  CK(cudaMemcpyAsync(out, d_out, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return HOM_OK;
 }

@@ -3,32 +3,12 @@
 #include <utility>
 
 #include "ls_common.cuh"
+#include "spectral.cuh"
 #include "zsplit.h"
 
 namespace hom {
 
 // ---------------------------------------------------------------------------------
-// zpass: one CTA per (tile of 2^tc_log2 spectrum columns, rhs)
-// Kelvin components -> symmetric tensor (t11, t22, t33, t23, t13, t12)
-template <typename T>
-__device__ __forceinline__ void kelvin_to_tensor(const cx<T>* k, cx<T>* t) {
-  const T r3 = (T)0.57735026918962576451, r2 = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637;
-  t[0] = k[0] * r3 + k[1] * r2 + k[2] * r6;
-  t[1] = k[0] * r3 - k[1] * r2 + k[2] * r6;
-  t[2] = k[0] * r3 - k[2] * ((T)2 * r6);
-  t[3] = k[3] * r2;
-  t[4] = k[4] * r2;
-  t[5] = k[5] * r2;
-}
-
-// w = t xi for a symmetric tensor t
-template <typename T>
-__device__ __forceinline__ void tensor_dot_xi(const cx<T>* t, T x1, T x2, T x3, cx<T>& w1, cx<T>& w2, cx<T>& w3) {
-  w1 = t[0] * x1 + t[5] * x2 + t[4] * x3;
-  w2 = t[5] * x1 + t[1] * x2 + t[3] * x3;
-  w3 = t[4] * x1 + t[3] * x2 + t[2] * x3;
-}
-
 // eta_hat = -Gamma0_hat(xi) : tau_hat in Kelvin components, given w = tau_hat xi.
 // Gamma0_hat : tau_hat = v (x) xi + xi (x) v with
 // v = w / (2 mu0 |xi|^2) - (lam0 + mu0) / (2 mu0 (lam0 + 2 mu0)) (xi . w) xi / |xi|^4,
@@ -58,13 +38,6 @@ __device__ __forceinline__ void green_from_w(cx<T>* k, cx<T> w1, cx<T> w2, cx<T>
   k[3] = (v2 * x3 + v3 * x2) * (-s2);
   k[4] = (v1 * x3 + v3 * x1) * (-s2);
   k[5] = (v1 * x2 + v2 * x1) * (-s2);
-}
-
-// integer wave number of DFT index j on an axis of length n, Nyquist -> 0 (discrete derivative)
-__device__ __forceinline__ int wave(int j, int n) {
-  int k = (j >= (n + 1) / 2) ? j - n : j;
-  if ((n & 1) == 0 && 2 * j == n) k = 0;
-  return k;
 }
 
 // Pointwise Green contraction of the split z pass: one thread per frequency and load, the six
@@ -120,6 +93,7 @@ template cudaError_t launch_zgreen<float>(const ZArgs<float>&, int, cudaStream_t
 template cudaError_t launch_zgreen<double>(const ZArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_zgreen<df64>(const ZArgs<df64>&, int, cudaStream_t);
 
+// zpass: one CTA per (tile of 2^tc_log2 spectrum columns, rhs)
 template <typename T, int EPT>
 __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
   const int tc_log2 = a.tc_log2;

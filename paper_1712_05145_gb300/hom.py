@@ -42,7 +42,7 @@ KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64",
                 "ypass", "ypass_f64"]
 
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
-            "hom_ls_apply", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
+            "hom_ls_apply", "hom_equilibrium_error", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
             "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
             "hom_server_create", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
             "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_launch_count", "hom_last_error",
@@ -124,6 +124,8 @@ def load_library(path=None):
     lib.hom_get_field.restype = I32
     lib.hom_ls_apply.argtypes = [V, I32, V, V, V]
     lib.hom_ls_apply.restype = I32
+    lib.hom_equilibrium_error.argtypes = [V, I32, V, V, V]
+    lib.hom_equilibrium_error.restype = I32
     lib.hom_fft_forward.argtypes = [V, I32, V, V]
     lib.hom_fft_forward.restype = I32
     lib.hom_fft_inverse.argtypes = [V, I32, V, V]
@@ -248,6 +250,15 @@ def hom_ls_apply(h, nrhs, eps_in, E, eps_out):
     E = None if E is None else np.ascontiguousarray(E, dtype=np.float64).reshape(nrhs, 6)
     _check(h, load_library().hom_ls_apply(h, int(nrhs), _ptr(eps_in), _ptr(E), _ptr(eps_out)))
     return eps_out
+
+
+def hom_equilibrium_error(h, nrhs, eps=None, E=None):
+    """Equilibrium error sqrt(<|div sigma|^2>) / |<sigma>| of sigma = C : (E + eps) per field, or
+    of the solved order-0 loads when eps is None (nrhs = their count)."""
+    E = None if (E is None or eps is None) else np.ascontiguousarray(E, dtype=np.float64).reshape(nrhs, 6)
+    out = np.zeros(int(nrhs), dtype=np.float64)
+    _check(h, load_library().hom_equilibrium_error(h, int(nrhs), _ptr(eps), _ptr(E), _ptr(out)))
+    return out
 
 
 def hom_fft_forward(h, nfield, f, fhat):
@@ -420,6 +431,10 @@ class Homogenization:
 
     def effective(self, order):
         return hom_effective(self.h, order, self.nloads[order])
+
+    def equilibrium_error(self):
+        """Equilibrium error of the solved order-0 loads (one value per load)."""
+        return hom_equilibrium_error(self.h, self.nloads.get(0, 0))
 
     def field(self, order, load, kind=HOM_FIELD_STRAIN, device=False):
         nc = 3 if kind == HOM_FIELD_DISPLACEMENT else 6

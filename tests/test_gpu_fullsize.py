@@ -2,8 +2,9 @@
 and properties that hold at any size on the 512^3 configuration.
 
 * One LS step at 128^3 against the oracle, every element.
-* The bench's solve: the oracle recomputes the FP64 residual of two GPU solutions with its own
-  operator; C_eff is symmetric and lies between the Reuss and Voigt bounds.
+* The bench's solve: the oracle recomputes the FP64 residual and the equilibrium error of two
+  GPU solutions with its own operator; C_eff is symmetric and lies between the Reuss and Voigt
+  bounds.
 * 512^3 Voronoi (256 grains): the reported FP64 residuals meet the tolerance, C_eff is symmetric
   and within the bounds of the voxel phase fractions.
 """
@@ -11,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import closed_forms
+from oracle import equilibrium
 from oracle.lippmann_schwinger import Problem
 from oracle.tensors import mandel_to_tensor, tensor_to_mandel, unit_mandel_load
 from paper_1712_05145_gb300 import synthetic
@@ -58,10 +60,14 @@ def test_bench_solve_residual_recomputed_by_oracle():
     assert all(i["status"] == 0 and i["rel_residual_fp64"] < BENCH_TOL for i in info), info
     c = H.effective(0)
     pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
+    eq_gpu = H.equilibrium_error()
     for a in (0, 3):
         E = unit_mandel_load(a)
         b = pb.rhs(E)
         eps = mandel_to_tensor(H.field(0, a))
+        # the equilibrium error of the GPU solution, by the GPU and by the oracle
+        eq_ref = equilibrium.equilibrium_error(equilibrium.stress_of(pb, eps, E), pb.grid)
+        assert abs(eq_gpu[a] - eq_ref) < 1e-3 * eq_ref, (a, eq_gpu[a], eq_ref)
         res = pb.residual(eps, b)
         # the oracle's FP64 residual of the GPU solution meets the tolerance and agrees with the
         # residual the library reported (both FP64, different code)
