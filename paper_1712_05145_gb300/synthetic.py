@@ -85,6 +85,18 @@ def midpoint_reference(lame):
             0.5 * (lame[:, 1].min() + lame[:, 1].max()))
 
 
+def geometric_reference(lame):
+    """Reference medium whose Kelvin moduli 3K0 and 2mu0 are the geometric means of the phases'
+    smallest and largest 3K and 2mu: the choice that minimises max |(c - c0) / (c + c0)|, the
+    contraction factor of the polarization scheme."""
+    lame = np.asarray(lame, dtype=np.float64)
+    k3 = 3.0 * lame[:, 0] + 2.0 * lame[:, 1]
+    m2 = 2.0 * lame[:, 1]
+    k30 = np.sqrt(k3.min() * k3.max())
+    m20 = np.sqrt(m2.min() * m2.max())
+    return (k30 - m20) / 3.0, 0.5 * m20
+
+
 @dataclass
 class Microstructure:
     phase: np.ndarray
