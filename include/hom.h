@@ -59,16 +59,22 @@ typedef enum {
 } hom_status;
 
 enum { HOM_FP64 = 0, HOM_FP32_REFINE = 1 };
-enum { HOM_BASIC = 0, HOM_CG = 1, HOM_BICGSTAB = 2 };
+enum { HOM_BASIC = 0, HOM_CG = 1, HOM_BICGSTAB = 2, HOM_POLARIZATION = 3 };
 enum { HOM_FIELD_STRAIN = 0, HOM_FIELD_DISPLACEMENT = 1, HOM_FIELD_STRESS = 2 };
 
 typedef struct {
   int32_t precision;       /* HOM_FP64: FP64 fields and FFTs.  HOM_FP32_REFINE: FP32 fields and
                               FFTs, FP64 reductions, FP64 residual-correction sweeps. */
-  int32_t scheme;          /* HOM_BASIC (fixed point), HOM_CG (CG on A eps = b, C0 product) or
+  int32_t scheme;          /* HOM_BASIC (fixed point), HOM_CG (CG on A eps = b, C0 product),
                               HOM_BICGSTAB (BiCGSTAB on A eps = b, L2 products; the solver the
                               paper ran for its CG-version, Sec. 4; iterations count full steps,
-                              each with two operator applications) */
+                              each with two operator applications) or HOM_POLARIZATION (the
+                              polarization scheme cited in Sec. 1: the fixed point
+                              x = b + (I - 2 Gamma0 * C0) W x, W = (C - C0)(C + C0)^-1,
+                              eps = (I - W) x, one LS pass per iteration; it contracts by
+                              max |(c - c0)/(c + c0)| over the phases' Kelvin moduli c, so C0
+                              near the geometric mean of the phases converges fastest.  Needs
+                              mu0 > 0, 3 lambda0 + 2 mu0 > 0 and non-negative phase moduli) */
   int32_t max_iter;        /* iteration cap per load (inner iterations in FP32_REFINE) */
   int32_t check_every;     /* iterations between host convergence checks (>= 1) */
   int32_t max_refine;      /* FP32_REFINE: cap on FP64 residual-correction sweeps */
@@ -84,7 +90,10 @@ typedef struct {
   int32_t autotune;        /* 1: before the first solve, time one operator application per
                               candidate launch shape (loads per launch, z-pass tile width) on
                               this grid and keep the fastest; 0 (default): fixed rules */
-  int32_t reserved[6];
+  int32_t polarization_variant; /* HOM_POLARIZATION: 0 = x <- T(x) (Eyre-Milton, Monchiet-Bonnet);
+                              1 = x <- (x + T(x)) / 2 (the averaged, augmented-Lagrangian form,
+                              which also converges where a phase modulus is 0) */
+  int32_t reserved[5];
 } hom_options;
 
 typedef struct {

@@ -3,6 +3,7 @@
     python -m paper_1712_05145_gb300.configs c1   # 32^3 sphere, FP64 Basic Scheme to 1e-8; 32^3 laminate
     python -m paper_1712_05145_gb300.configs c3   # 3-phase spheres, orders 0, 1, 2 at 64^3 and 128^3
     python -m paper_1712_05145_gb300.configs c5   # 512^3 periodic Voronoi of 256 grains, order 0
+    python -m paper_1712_05145_gb300.configs schemes   # C2's RVE: CG, polarization, BiCGSTAB, Basic
 
 Each prints one JSON line per case: iterations, device time per order, voxel-iterations per
 second and the effective tensors.  Parity of these workloads with the CPU oracle is checked by
@@ -11,6 +12,8 @@ the test suite on sizes the oracle finishes.
 import argparse
 import json
 import time
+
+import numpy as np
 
 
 def _timed(fn):
@@ -98,9 +101,39 @@ def run_c5(n=512):
                       "max_rel_difference": float(np.abs(c512 - c128).max() / np.abs(c512).max())}), flush=True)
 
 
+def run_schemes(n=128):
+    """The C2 microstructure (random spheres, contrast 100, 6 unit loads, tol 1e-6) solved by each
+    scheme in both precisions; the polarization scheme with the geometric-mean reference medium,
+    the others with the midpoint reference."""
+    from paper_1712_05145_gb300 import hom, synthetic
+    ms = synthetic.random_spheres((n, n, n), seed=1713)
+    geo = synthetic.geometric_reference(ms.lame)
+    cases = [("CG", hom.HOM_CG, 0, None), ("BiCGSTAB", hom.HOM_BICGSTAB, 0, None),
+             ("polarization (Eyre-Milton)", hom.HOM_POLARIZATION, 0, geo),
+             ("polarization (augmented Lagrangian)", hom.HOM_POLARIZATION, 1, geo),
+             ("Basic Scheme", hom.HOM_BASIC, 0, None)]
+    for precision in (hom.HOM_FP32_REFINE, hom.HOM_FP64):
+        for name, scheme, variant, ref in cases:
+            if scheme == hom.HOM_BASIC and precision == hom.HOM_FP32_REFINE:
+                continue   # the Basic Scheme does not refine: its FP32 result stops at FP32 accuracy
+            kw = {} if ref is None else {"lam0": ref[0], "mu0": ref[1]}
+            H = hom.Homogenization(ms, precision=precision, scheme=scheme, polarization_variant=variant,
+                                   max_iter=20000, **kw)
+            H.solve(0, 1e-6, loads=np.eye(6)[:1])        # warm-up (allocation, tables)
+            info, dt = _timed(lambda: H.solve(0, 1e-6))
+            it = sum(i["iterations"] for i in info)
+            print(json.dumps({"config": "C2 RVE %d^3, 6 loads, tol 1e-6" % n, "scheme": name,
+                              "precision": "fp32+refine" if precision == hom.HOM_FP32_REFINE else "fp64",
+                              "iterations": it, "seconds": dt, "voxel_iters_per_s": n ** 3 * it / dt,
+                              "max_rel_residual_fp64": max(i["rel_residual_fp64"] for i in info),
+                              "ok": all(i["status"] == 0 for i in info),
+                              "c11": float(H.effective(0)[0, 0])}), flush=True)
+            H.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("config", choices=["c1", "c3", "c5"])
+    ap.add_argument("config", choices=["c1", "c3", "c5", "schemes"])
     ap.add_argument("--grid", type=int, default=0)
     args = ap.parse_args()
     from paper_1712_05145_gb300 import build
@@ -109,6 +142,8 @@ def main():
         run_c1()
     elif args.config == "c3":
         run_c3((args.grid,) if args.grid else (64, 128))
+    elif args.config == "schemes":
+        run_schemes(args.grid or 128)
     else:
         run_c5(args.grid or 512)
 

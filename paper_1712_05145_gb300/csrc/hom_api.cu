@@ -19,6 +19,7 @@
 #include "aux.h"
 #include "equilibrium.h"
 #include "hierarchy.h"
+#include "polarization.h"
 #include "zsplit.h"
 #include "hom.h"
 #include "internal.h"
@@ -104,7 +105,10 @@ struct hom_ctx {
   void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};
   int ztile_lg[2] = {-1, -1};  // z-pass tile width forced by the autotuner (FP32, FP64); -1: rule
   bool tuned = false;
-  void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t
+  void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t (the polarization scheme: eta)
+  std::vector<double> kelvin;  // [n_phase][4] host copy of the material table: C - C0, C
+  double* d_polar64 = nullptr; // [n_phase][4] polarization-scheme table (c0 w, w), built on first use
+  float* d_polar32 = nullptr;
   size_t bicg_bytes = 0;
   size_t work_bytes[4] = {0, 0, 0, 0};
   OrderData ord[kMaxOrder + 1];
@@ -653,6 +657,104 @@ hom_status bicgstab_sweep(hom_ctx* c, int n, Tf* x, Tf* r, Tf* p, std::vector<Rh
   return HOM_OK;
 }
 
+// Per-phase table of the polarization scheme, [n_phase][4] in Kelvin eigenvalues: c0 w and w for
+// the hydrostatic and the deviatoric modes, w = (c - c0) / (c + c0) = eigenvalue of
+// W = (C - C0) (C + C0)^-1.  The first two entries take the place of C - C0 in a FWD_TAU pass,
+// which then transforms C0 : W x.
+template <typename Tf> Tf*& polar_table_slot(hom_ctx* c);
+template <> float*& polar_table_slot<float>(hom_ctx* c) { return c->d_polar32; }
+template <> double*& polar_table_slot<double>(hom_ctx* c) { return c->d_polar64; }
+template <typename Tf>
+hom_status polar_table(hom_ctx* c, const Tf** out) {
+  Tf*& slot = polar_table_slot<Tf>(c);
+  if (!slot) {
+    const double c0[2] = {3.0 * c->lam0 + 2.0 * c->mu0, 2.0 * c->mu0};
+    std::vector<Tf> t(4 * 256, (Tf)0);
+    for (int i = 0; i < c->nphase; ++i) {
+      for (int m = 0; m < 2; ++m) {
+        const double cp = c->kelvin[4 * i + 2 + m];
+        const double w = (cp - c0[m]) / (cp + c0[m]);
+        t[4 * i + m] = (Tf)(c0[m] * w);
+        t[4 * i + 2 + m] = (Tf)w;
+      }
+    }
+    void* p;
+    CKS(dalloc(c, &p, sizeof(Tf) * 4 * 256));
+    slot = reinterpret_cast<Tf*>(p);
+    CK(cudaMemcpyAsync(slot, t.data(), sizeof(Tf) * 4 * 256, cudaMemcpyHostToDevice, c->stream));
+  }
+  *out = slot;
+  return HOM_OK;
+}
+
+// One polarization-scheme sweep on A d' = r (Eq. cg_form) for the active loads, from x = r:
+//   x <- (1 - g) x + g (r + W x + 2 eta),  eta = -Gamma0 * (C0 : W x)  (an LS pass),
+// until each load's Cauchy quantity ||(I - W)(x_{k+1} - x_k)|| / ||b|| meets its tolerance; then
+// d += (I - W) x for the loads that ran.  x lives in the p buffer, eta in the BiCGSTAB scratch.
+template <typename Tf>
+hom_status polar_sweep(hom_ctx* c, int n, Tf* d, const Tf* r, Tf* x, std::vector<RhsState>& st,
+                       std::vector<int>& act) {
+  const size_t fb = tbytes<Tf>(c, n, 6);
+  if (c->bicg_bytes < fb) {
+    if (c->d_bicg) dfree(c, c->d_bicg, c->bicg_bytes);
+    c->d_bicg = nullptr;
+    c->bicg_bytes = 0;
+    CKS(dalloc(c, &c->d_bicg, fb));
+    c->bicg_bytes = fb;
+  }
+  const Tf* wt;
+  CKS(polar_table<Tf>(c, &wt));
+  CK(cudaMemcpyAsync(x, r, fb, cudaMemcpyDeviceToDevice, c->stream));
+  PolarArgs<Tf> a;
+  a.x = x;
+  a.r = r;
+  a.eta = reinterpret_cast<const Tf*>(c->d_bicg);
+  a.d = d;
+  a.phase = c->d_phase;
+  a.wt = wt;
+  a.n_phase = c->nphase;
+  a.relax = (c->opt.polarization_variant == 1) ? 0.5 : 1.0;
+  a.M = c->g.M;
+  a.rhs0 = 0;
+  a.st = c->d_st;
+  a.part = part_fwd(c);
+  a.pstride = (int)ncta_max(c);
+  a.cnt = cnt_fwd(c);
+  const int nblk = std::max(1, std::min(a.pstride, std::max(64, (152 * 8) / n)));
+  const std::vector<int> ran = act;
+  bool any = true;
+  while (any) {
+    for (int k = 0; k < c->opt.check_every; ++k) {
+      auto fa = fwd_args<Tf, Tf>(c, FWD_TAU, 6, 6);
+      fa.mat = wt;
+      fa.in = x;
+      fa.st = c->d_st;
+      auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
+      za.st = c->d_st;
+      auto ia = inv_args<Tf, Tf>(c, INV_STORE, FIN_NONE, 6, 6, 6);
+      ia.out = reinterpret_cast<Tf*>(c->d_bicg);
+      ia.st = c->d_st;
+      CKS((ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia, &act)));
+      CK(launch_polar<Tf>(PO_UPDATE, a, n, nblk, c->stream));
+    }
+    CKS(read_states(c, n, st));
+    any = false;
+    for (int i = 0; i < n; ++i) {
+      act[i] = st[i].active;
+      any = any || act[i];
+    }
+  }
+  for (int i0 = 0; i0 < n;) {   // d += (I - W) x over each run of loads that took part
+    if (!ran[i0]) { ++i0; continue; }
+    int i1 = i0;
+    while (i1 < n && ran[i1]) ++i1;
+    a.rhs0 = i0;
+    CK(launch_polar<Tf>(PO_FINISH, a, i1 - i0, nblk, c->stream));
+    i0 = i1;
+  }
+  return HOM_OK;
+}
+
 // FP64 residual of the operator of Eq. cg_form itself, r = b - A x with A = Id + Gamma0 * (C - C0):
 // one LS pass, tau = (C - C0) : (x + E), r = -Gamma0 * tau + b - x (for order 0, b is the E term
 // inside tau).  Unlike residual_sweep it sees an incompatible part of x, so a value below tol
@@ -700,6 +802,7 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   Tf* d = mixed ? reinterpret_cast<Tf*>(vd) : reinterpret_cast<Tf*>(x64);
   const bool basic = (c->opt.scheme == HOM_BASIC);
   const bool bicg = (c->opt.scheme == HOM_BICGSTAB);
+  const bool polar = (c->opt.scheme == HOM_POLARIZATION);
   // an FP32 sweep is asked for a reduction FP32 can deliver relative to its starting residual
   // The first sweep starts from b and aims at the tolerance itself where FP32 can reach it
   // (relative residuals down to kFirstSweepFloor); later sweeps ask for kSweepGain relative to
@@ -716,7 +819,9 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   //    projected x (two FP64 passes).  The first sweep aims only at kFirstSweepTarget: the
   //    projection after it perturbs the residual by about the incompatible part anyway, and the
   //    later sweeps, whose corrections are small, leave a negligible incompatible part.
-  const bool project = mixed;
+  // The polarization scheme's iterates are compatible only at the fixed point, so it takes the
+  // same verification in both precisions.
+  const bool project = mixed || polar;
 
   std::vector<RhsState> st(n);
   for (int i = 0; i < n; ++i) {
@@ -828,6 +933,10 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
       for (int i = 0; i < n; ++i) any = any || act[i];
       if (bicg && any) {
         CKS(bicgstab_sweep<Tf>(c, n, d, r, p, st, act));
+        any = false;
+      }
+      if (polar && any) {
+        CKS(polar_sweep<Tf>(c, n, d, r, p, st, act));
         any = false;
       }
       while (any) {
@@ -1419,9 +1528,21 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if (c->opt.max_refine < 0) c->opt.max_refine = 0;
   if (c->opt.spectrum_budget_bytes <= 0) c->opt.spectrum_budget_bytes = 1024LL << 20;
   if (c->opt.precision != HOM_FP64 && c->opt.precision != HOM_FP32_REFINE) { delete c; return HOM_ERR_ARG; }
-  if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG && c->opt.scheme != HOM_BICGSTAB) {
+  if (c->opt.scheme != HOM_BASIC && c->opt.scheme != HOM_CG && c->opt.scheme != HOM_BICGSTAB &&
+      c->opt.scheme != HOM_POLARIZATION) {
     delete c;
     return HOM_ERR_ARG;
+  }
+  if (c->opt.scheme == HOM_POLARIZATION) {
+    // |w| = |c - c0| / (c + c0) <= 1 needs positive reference moduli and non-negative phase moduli
+    bool ok = (mu0 > 0.0) && (3.0 * lambda0 + 2.0 * mu0 > 0.0) &&
+              (c->opt.polarization_variant == 0 || c->opt.polarization_variant == 1);
+    for (int i = 0; i < n_phase && ok; ++i)
+      ok = (2.0 * lame[2 * i + 1] >= 0.0) && (3.0 * lame[2 * i] + 2.0 * lame[2 * i + 1] >= 0.0);
+    if (!ok) {
+      delete c;
+      return HOM_ERR_ARG;
+    }
   }
   c->fp32 = (c->opt.precision == HOM_FP32_REFINE);
   c->nphase = n_phase;
@@ -1484,6 +1605,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     m64[4 * i + 3] = 2.0 * m;
     for (int j = 0; j < 4; ++j) m32[4 * i + j] = (float)m64[4 * i + j];
   }
+  c->kelvin.assign(m64.begin(), m64.begin() + 4 * n_phase);
   if ((s = dalloc(c, (void**)&c->d_mat64, sizeof(double) * 4 * 256)) != HOM_OK) return bail(s);
   if ((s = dalloc(c, (void**)&c->d_mat32, sizeof(float) * 4 * 256)) != HOM_OK) return bail(s);
   cudaMemcpy(c->d_mat64, m64.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice);

@@ -30,6 +30,7 @@ HOM_FP32_REFINE = 1
 HOM_BASIC = 0
 HOM_CG = 1
 HOM_BICGSTAB = 2
+HOM_POLARIZATION = 3
 HOM_FIELD_STRAIN = 0
 HOM_FIELD_DISPLACEMENT = 1
 HOM_FIELD_STRESS = 2
@@ -53,7 +54,8 @@ class hom_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("scheme", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
                 ("spectrum_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-                ("pass_mode", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("pass_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("polarization_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -394,7 +396,7 @@ class Homogenization:
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
                  max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,
-                 pass_mode=0, autotune=0):
+                 pass_mode=0, autotune=0, polarization_variant=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
         self.M = n1 * n2 * n3
@@ -409,6 +411,7 @@ class Homogenization:
         opt.cuda_stream = stream
         opt.pass_mode = pass_mode
         opt.autotune = autotune
+        opt.polarization_variant = polarization_variant
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
                             ms.mu0 if mu0 is None else mu0, opt)
         self.nloads = {}
