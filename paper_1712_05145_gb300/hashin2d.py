@@ -10,9 +10,10 @@ Problems, as in Sec. 4 (the paper's numbering):
 * second-order problem: the alpha = 2 problem for (grad E)_111 = (grad E)_222 = 1.  It needs the
   first-order correctors of the unit strains e11 and e22, so its time includes that solve
   (both loads batched in one launch sequence) plus the alpha = 2 solve of the combined load.
-The schemes run in FP64 with the paper's tolerance 1e-6: the Basic Scheme (FFTH), CG and
+The schemes run in FP64 with the paper's tolerance 1e-6: the Basic Scheme (FFTH), CG,
 BiCGSTAB (the paper's CG-version ran MATLAB's BiCGSTAB; one BiCGSTAB iteration applies the
-operator twice).  Each line is one JSON object.
+operator twice) and the polarization scheme of Sec. 1's references (Eyre-Milton, with the
+geometric-mean reference medium).  Each line is one JSON object.
 """
 import argparse
 import json
@@ -25,7 +26,7 @@ E_ID = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 0.0]])
 W_111_222 = np.zeros((1, 18))
 W_111_222[0, 3 * 0 + 0] = 1.0   # E^(11) varying along Y1
 W_111_222[0, 3 * 1 + 1] = 1.0   # E^(22) varying along Y2
-SCHEMES = (("basic", 0), ("cg", 1), ("bicgstab", 2))   # HOM_BASIC, HOM_CG, HOM_BICGSTAB
+SCHEMES = (("basic", 0), ("cg", 1), ("bicgstab", 2), ("polarization", 3))   # hom.HOM_* schemes
 
 
 def _sync():
@@ -35,8 +36,11 @@ def _sync():
 
 def run_problems(ms, scheme, max_iter, repeat=1):
     """Iterations and device-synchronised wall times of the first- and second-order problems."""
-    from paper_1712_05145_gb300 import hom
-    H = hom.Homogenization(ms, precision=hom.HOM_FP64, scheme=scheme, max_iter=max_iter)
+    from paper_1712_05145_gb300 import hom, synthetic
+    kw = {}
+    if scheme == hom.HOM_POLARIZATION:   # its reference medium: geometric means of the phases
+        kw["lam0"], kw["mu0"] = synthetic.geometric_reference(ms.lame)
+    H = hom.Homogenization(ms, precision=hom.HOM_FP64, scheme=scheme, max_iter=max_iter, **kw)
     out = {}
     best1 = best2 = None
     for _ in range(repeat):

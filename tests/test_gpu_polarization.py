@@ -107,3 +107,20 @@ def test_expanding_arguments_are_rejected():
         with pytest.raises(hom.HomError) as e:
             hom.Homogenization(ms, scheme=hom.HOM_POLARIZATION, lam0=lam0, mu0=mu0, polarization_variant=variant)
         assert e.value.status == hom.HOM_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_split_passes_match_fused(precision):
+    """The polarization sweep through the split x and y passes gives the fused kernels' result."""
+    from paper_1712_05145_gb300 import hom
+    ms = cell((16, 12, 6), 59)
+    tol = 1e-12 if precision == 0 else 1e-9
+    out = []
+    for pass_mode in (1, 2):
+        H = hom.Homogenization(ms, precision=precision, scheme=hom.HOM_POLARIZATION, pass_mode=pass_mode)
+        info = H.solve(0, tol)
+        assert all(i["status"] == 0 for i in info), info
+        out.append((H.effective(0), H.field(0, 2)))
+        H.close()
+    assert rel_err(out[1][0], out[0][0]) < TOL_EFF[precision]
+    assert rel_err(out[1][1], out[0][1]) < TOL[precision]
