@@ -67,6 +67,23 @@ def test_bad_reference_medium_rejected(lib):
         assert e.value.status == hom.HOM_ERR_ARG
 
 
+def test_polarization_scheme_rejects_expanding_arguments(lib):
+    """The polarization scheme contracts only for positive reference moduli and non-negative
+    phase moduli; anything else, and an unknown variant, is refused before any CUDA call."""
+    phase = np.zeros((8, 8, 8), dtype=np.uint8)
+    cases = [((1.0, 1.0), 1.0, -0.5, 0),     # mu0 < 0
+             ((1.0, 1.0), -1.0, 0.4, 0),     # 3 lam0 + 2 mu0 < 0
+             ((-1.0, 0.2), 1.0, 1.0, 0),     # a phase with 3K < 0
+             ((1.0, 1.0), 1.0, 1.0, 2)]      # unknown variant
+    for (lam, mu), lam0, mu0, variant in cases:
+        opt = hom.hom_default_options()
+        opt.scheme = hom.HOM_POLARIZATION
+        opt.polarization_variant = variant
+        with pytest.raises(hom.HomError) as e:
+            hom.hom_create((8, 8, 8), phase, np.array([[lam, mu]]), lam0, mu0, opt)
+        assert e.value.status == hom.HOM_ERR_ARG
+
+
 def test_null_handle_calls(lib):
     assert lib.hom_solve(None, 0, 6, None, 1e-6, None) == hom.HOM_ERR_ARG
     assert lib.hom_effective(None, 0, None) == hom.HOM_ERR_ARG
