@@ -19,12 +19,12 @@
  *  - Symmetric tensors are Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12);
  *    vectors are 3 components (x1, x2, x3).  6x6 and 6xK matrices are row-major.
  *  - Orders are counted from 0: order 0 is the classical cell problem (the paper's
- *    alpha = 1), order o >= 1 is the paper's alpha = o + 1 (orders up to 4).
+ *    alpha = 1), order o >= 1 is the paper's alpha = o + 1 (orders up to 6).
  *  - Unit loads: order 0, load A = 0..5 is the Mandel unit strain E^A; order 1,
  *    load 3*A + k is E(Y) = E^A Y_k (18 loads); order 2, load 6*A + P is
  *    E(Y) = E^A Y_k Y_l / (1 + delta_kl) with (k, l) the P-th Mandel pair (36 loads);
  *    order o >= 3, E(Y) = E^A Y^K / K! for the multisets K of o directions in
- *    lexicographic order (60 loads for o = 3, 90 for o = 4).
+ *    lexicographic order (6 (o+1)(o+2)/2 loads: 60, 90, 126, 168 for o = 3 to 6).
  *  - Spectral operators use the discrete wave vector xi_i = 2 pi k_i / (N_i h) with the
  *    Nyquist component (k_i = N_i/2 on even axes) taken as 0.
  *  - Errors are returned as hom_status; no C++ exception crosses the ABI.  After an
@@ -127,7 +127,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
                               const double* lame, double lambda0, double mu0,
                               const hom_options* opt, hom_t* out);
 
-/* Solves problem `order` (0 to 4: the paper's alpha = order + 1) for its loads to relative
+/* Solves problem `order` (0 to 6: the paper's alpha = order + 1) for its loads to relative
  * residual tol:
  * ||b - A eps||_L2 / ||b||_L2 < tol with A = Id + Gamma0 * (C - C0) (Eq. cg_form); for the
  * Basic Scheme this is the paper's Cauchy quantity ||eps_{n+1} - eps_n|| / ||eps_0||.
@@ -139,7 +139,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
  *           Every unit load used needs the unit strain e_A among the converged order-0 loads.
  *  order o >= 2: requires order o - 1 solved for its unit loads; loads must be NULL.  The unit
  *           loads are E(Y) = E^A Y^K / K! for the multisets K of o directions: 6 x (o+1)(o+2)/2
- *           loads (36, 60, 90 for o = 2, 3, 4), load A * nK + (index of K), K ordered as the
+ *           loads (36, 60, 90, 126, 168 for o = 2 to 6), load A * nK + (index of K), K ordered as the
  *           Mandel pairs (11, 22, 33, 23, 13, 12) for o = 2 and lexicographically (sorted
  *           tuples, 111 < 112 < ... < 333) for o >= 3.
  *  info     host array of one hom_solve_info per load (nullable); caller-owned.
@@ -253,7 +253,7 @@ HOM_API hom_status hom_ls_apply_noalloc(const int32_t grid[3], const uint8_t* ph
 /* Text of the calling thread's last hom_ls_apply_noalloc error ("" after a success). */
 HOM_API const char* hom_noalloc_last_error(void);
 
-/* Device bytes a handle with default options needs to solve `order` (0 or 1) on this grid in
+/* Device bytes a handle with default options needs to solve `order` (0 to 6) on this grid in
  * `precision`, as counted from its allocations (used for admission by the server); -1 if the
  * grid is not supported. */
 HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision);

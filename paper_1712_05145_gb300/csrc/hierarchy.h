@@ -23,8 +23,8 @@ struct UnitMap {
   int unit[18];
   int a0[6];
 };
-constexpr int kMaxOrder = 4;     // orders 0..4 (the paper's alpha = 1..5)
-constexpr int kMaxMultisets = 15;
+constexpr int kMaxOrder = 6;     // orders 0..6 (the paper's alpha = 1..7)
+constexpr int kMaxMultisets = 28; // multisets of 6 directions from 3: (6 + 1)(6 + 2) / 2
 struct RecTable {
   int nK, nKprev;                  // multisets of this order and of the previous one
   int nterm[kMaxMultisets];

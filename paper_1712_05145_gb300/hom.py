@@ -392,7 +392,6 @@ class Homogenization:
     """One RVE on the GPU.  ``ms`` is a synthetic.Microstructure (or anything with
     .phase, .lame, .lam0, .mu0)."""
 
-    NLOADS = {0: 6, 1: 18, 2: 36}
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
                  max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,

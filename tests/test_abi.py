@@ -93,7 +93,9 @@ def test_null_handle_calls(lib):
 
 def test_estimate_accepts_two_dimensional_cells_and_rejects_empty_axes(lib):
     assert hom.hom_estimate_bytes((64, 64, 1), 0) > 0
-    assert hom.hom_estimate_bytes((64, 64, 1), 4) > hom.hom_estimate_bytes((64, 64, 1), 3)
+    for o in range(1, 7):
+        assert hom.hom_estimate_bytes((64, 64, 1), o) > hom.hom_estimate_bytes((64, 64, 1), o - 1)
     for g in [(0, 8, 8), (8, 0, 8), (8, 8, 0), (8, 1, 8), (1, 8, 8)]:
         assert hom.hom_estimate_bytes(g, 0) < 0
-    assert hom.hom_estimate_bytes((8, 8, 8), 5) < 0
+    assert hom.hom_estimate_bytes((8, 8, 8), 7) < 0
+    assert hom.hom_estimate_bytes((8, 8, 8), -1) < 0

@@ -1,4 +1,4 @@
-"""GPU parity of the higher-order problems (orders 1 and 2, the paper's alpha = 2 and 3)."""
+"""GPU parity of the higher-order problems (orders 1 to 6, the paper's alpha = 2 to 7)."""
 import numpy as np
 import pytest
 
@@ -122,4 +122,61 @@ def test_order3_vanishes_for_centrosymmetric_cell():
         assert all(i["status"] == 0 for i in info)
     assert np.abs(H.effective(3)).max() < 1e-9 * np.abs(H.effective(2)).max()
     assert np.abs(H.effective(2)).max() > 1e-4
+    H.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_general_small():
+    """An asymmetric three-phase 4 x 6 x 4 cell with the oracle's orders up to alpha = 7."""
+    from oracle.hierarchy import GeneralHierarchy
+    g = (4, 6, 4)
+    ms = synthetic.Microstructure(random_phase(g, 3, 23, p=[0.5, 0.3, 0.2]),
+                                  np.array([[1.0, 1.0], [6.0, 4.0], [0.3, 0.2]]), 3.0, 2.0)
+    h = Hierarchy(Problem(ms.phase, ms.lame, ms.lam0, ms.mu0), tol=1e-12)
+    h.order1()
+    h.order2()
+    G = GeneralHierarchy(h)
+    for alpha in range(2, 8):
+        G.solve(alpha)
+    return ms, G
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_orders_5_and_6_match_oracle(oracle_general_small, precision):
+    """Orders 5 and 6 (the paper's alpha = 6, 7): 126 and 168 unit loads."""
+    from oracle.hierarchy import multisets
+    from paper_1712_05145_gb300 import hom
+    ms, G = oracle_general_small
+    H = hom.Homogenization(ms, precision=precision)
+    tol = 1e-12 if precision == 0 else 1e-9
+    for order in range(7):
+        info = H.solve(order, tol)
+        assert len(info) == hom.loads_of_order(order)
+        assert all(i["status"] == 0 for i in info), (order, info)
+    tol_f = TOL[precision] * (1 if precision == 0 else 10)
+    for order in (5, 6):
+        D = H.effective(order)
+        assert D.shape == (6, hom.loads_of_order(order))
+        assert rel_err(D, G.D[order + 1]) < TOL_EFF[precision] * 10, order
+        Ks = multisets(order)
+        for L in (0, len(Ks) + 5, 6 * len(Ks) - 1):
+            a, k = divmod(L, len(Ks))
+            ref = tensor_to_mandel(G.eps[order + 1][(a, Ks[k])])
+            assert rel_err(H.field(order, L), ref) < tol_f, (order, L)
+    with pytest.raises(hom.HomError) as e:
+        H.solve(7, tol)
+    assert e.value.status == hom.HOM_ERR_ARG
+    H.close()
+
+
+def test_order5_vanishes_for_centrosymmetric_cell():
+    """D5 (alpha = 6) is an odd-order tensor: zero for a centrosymmetric cell, like D1 and D3."""
+    from paper_1712_05145_gb300 import hom
+    ms = synthetic.centred_sphere(8)
+    H = hom.Homogenization(ms, precision=0)
+    for order in range(6):
+        info = H.solve(order, 1e-12)
+        assert all(i["status"] == 0 for i in info)
+    assert np.abs(H.effective(5)).max() < 1e-9 * np.abs(H.effective(4)).max()
+    assert np.abs(H.effective(4)).max() > 1e-6
     H.close()
