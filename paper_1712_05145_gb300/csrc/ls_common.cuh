@@ -23,16 +23,16 @@ constexpr int kEPT = 16;
 // to 512 threads.  (8 elements per thread with 1024-thread CTAs and 32 registers, which doubles
 // the resident warps, measured slower at 128^3: the extra radix stage and register spills cost
 // more than the occupancy gained.)  kBatch: elements per thread whose global loads the prologue
-// and epilogue loops issue together; kSBatch: the same for the spectrum read of plane_inv.
+// and epilogue loops issue together.
 template <typename T> struct PlaneCfg;
 template <> struct PlaneCfg<float> {   // 64 registers: 2 CTAs per SM
-  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 2, kBatch = 4, kSBatch = 8;
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 2, kBatch = 4;
 };
 template <> struct PlaneCfg<double> {
-  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4;
 };
 template <> struct PlaneCfg<df64> {
-  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4, kSBatch = 8;
+  static constexpr int kEPT = 16, kMaxThreads = 512, kMinBlocks = 1, kBatch = 4;
 };
 // threads of a plane CTA: every element of the n2 x h plane has a slot, whole warps, >= 128
 template <typename T>
@@ -71,6 +71,19 @@ __device__ __forceinline__ void st2(Tf* p, Tf a, Tf b) {
 }
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Asynchronous global -> shared copy of one complex value (cp.async, 8 or 16 bytes, both
+// addresses aligned to it): a CTA's copies of a whole tile are in flight together without
+// staging registers.  cp_async_wait_all commits them and waits for all of this thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  static_assert(BYTES == 8 || BYTES == 16, "cp.async copies 8 or 16 bytes here");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 
 // Bulk prefetch of a contiguous global range into L2 (TMA, sm_90+).  bytes must be a multiple
 // of 16 and ptr 16-byte aligned; the range must lie inside one allocation.  Issued by one thread.

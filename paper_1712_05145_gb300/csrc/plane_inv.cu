@@ -43,11 +43,21 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
       }
     }
   }
+  // the spectrum plane (contiguous, row pitch h: flat index e = row * h + col) goes to shared
+  // memory (row pitch P) by cp.async while the twiddle tables load; the Nyquist column kx = n1/2
+  // lands in the n2 slots after the plane
+  const cx<T>* Sp = a.S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
+  const int nmain = n2 * h;
+  cx<T>* nyq = pl + n2 * P;
+  for (int e = tid; e < nmain; e += nthr) {
+    const int row = (int)g.fd_h.div((unsigned)e), col = e - row * h;
+    cp_async_elem<sizeof(cx<T>)>(pl + row * P + col, Sp + e);
+  }
+  for (int ky = tid; ky < n2; ky += nthr) cp_async_elem<sizeof(cx<T>)>(nyq + ky, Sp + nmain + ky);
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
 
-  const cx<T>* Sp = a.S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
   if (a.prof != nullptr && tid == 0) {
     const long long psz = (long long)n2 * n1;
     long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
@@ -57,29 +67,11 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)psz);
   }
-  const int nmain = n2 * h;
-  // the spectrum plane is contiguous (row pitch h): flat index e = row * h + col; kSBatch
-  // loads of a thread are in flight together
-  constexpr int kSBatch = PlaneCfg<T>::kSBatch;
-  for (int e0 = tid; e0 < nmain; e0 += kSBatch * nthr) {
-    cx<T> v[kSBatch];
-    #pragma unroll
-    for (int j = 0; j < kSBatch; ++j) {
-      const int e = e0 + j * nthr;
-      if (e < nmain) v[j] = Sp[e];
-    }
-    #pragma unroll
-    for (int j = 0; j < kSBatch; ++j) {
-      const int e = e0 + j * nthr;
-      if (e < nmain) {
-        const int row = (int)g.fd_h.div((unsigned)e), col = e - row * h;
-        if (col == 0) {  // pack kx = 0 (A) and kx = n1/2 (B) as A + i B
-          const cx<T> b = Sp[nmain + row];
-          v[j] = mk<T>(v[j].re - b.im, v[j].im + b.re);
-        }
-        pl[row * P + col] = v[j];
-      }
-    }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int row = tid; row < n2; row += nthr) {   // pack kx = 0 (A) and kx = n1/2 (B) as A + i B
+    const cx<T> v = pl[row * P], b = nyq[row];
+    pl[row * P] = mk<T>(v.re - b.im, v.im + b.re);
   }
   __syncthreads();
 

@@ -117,31 +117,16 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
 
   const int per_c = n3 * TC;
   {
-    // kZBatch loads per thread in flight together, then the shared-memory stores
-    constexpr int kZBatch = 8;
+    // the whole tile is in flight at once: cp.async per element, zeros past the last column
     const int total = a.ncomp_in * per_c;
-    for (int e0 = tid; e0 < total; e0 += kZBatch * nthr) {
-      cx<T> v[kZBatch];
-      #pragma unroll
-      for (int j = 0; j < kZBatch; ++j) {
-        const int e = e0 + j * nthr;
-        v[j] = mk<T>(0, 0);
-        if (e < total) {
-          const int c = (int)a.fd_comp.div((unsigned)e), ec = e - c * per_c;
-          const int tc = ec & (TC - 1), n = ec >> tc_log2;
-          const long long f = f0 + tc;
-          if (f < g.plane_c) v[j] = Sr[(long long)(c * n3 + n) * g.plane_c + f];
-        }
-      }
-      #pragma unroll
-      for (int j = 0; j < kZBatch; ++j) {
-        const int e = e0 + j * nthr;
-        if (e < total) {
-          const int c = (int)a.fd_comp.div((unsigned)e);
-          buf[c * cstride + e - c * per_c] = v[j];
-        }
-      }
+    for (int e = tid; e < total; e += nthr) {
+      const int c = (int)a.fd_comp.div((unsigned)e), ec = e - c * per_c;
+      const int tc = ec & (TC - 1), n = ec >> tc_log2;
+      const long long f = f0 + tc;
+      if (f < g.plane_c) cp_async_elem<sizeof(cx<T>)>(buf + c * cstride + ec, Sr + (long long)(c * n3 + n) * g.plane_c + f);
+      else buf[c * cstride + ec] = mk<T>(0, 0);
     }
+    cp_async_wait_all();
   }
   __syncthreads();
   const ZAddr za{tc_log2, cstride, TC};
