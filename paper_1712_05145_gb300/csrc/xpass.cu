@@ -156,10 +156,21 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
   int* flag = reinterpret_cast<int*>(sh + 64);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  // the block's spectrum rows go to shared memory by cp.async while the twiddle tables load
+  const cx<T>* Sc = a.S + (long long)(lrhs * a.s_ncomp + c) * g.n3 * g.plane_c;
+#pragma unroll 4
+  for (int lr = warp; lr < rb; lr += nwarp) {
+    if (lr < nr) {
+      const unsigned gr = (unsigned)(r0 + lr);
+      const unsigned zz = g.fd_n2.div(gr), yy = gr - zz * (unsigned)g.n2;
+      const cx<T>* src = Sc + (long long)zz * g.plane_c + (long long)yy * h;
+      for (int col = lane; col < h; col += 32) cp_async_elem<sizeof(cx<T>)>(pl + lr * P + col, src + col);
+    } else {
+      for (int col = lane; col < h; col += 32) pl[lr * P + col] = mk<T>(0, 0);
+    }
+  }
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
-
-  const cx<T>* Sc = a.S + (long long)(lrhs * a.s_ncomp + c) * g.n3 * g.plane_c;
   if (a.prof != nullptr && tid == 0) {
     const long long vox = (long long)nr * n1;
     long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
@@ -169,13 +180,7 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)vox);
   }
-#pragma unroll 4
-  for (int lr = warp; lr < rb; lr += nwarp) {
-    const unsigned gr = (unsigned)(r0 + (lr < nr ? lr : 0));
-    const unsigned zz = g.fd_n2.div(gr), yy = gr - zz * (unsigned)g.n2;
-    const cx<T>* src = Sc + (long long)zz * g.plane_c + (long long)yy * h;
-    for (int col = lane; col < h; col += 32) pl[lr * P + col] = (lr < nr) ? src[col] : mk<T>(0, 0);
-  }
+  cp_async_wait_all();
   __syncthreads();
 
   // C2R merge (as in plane_inv); slot 0 holds X[0] + i X[n1/2]

@@ -22,24 +22,28 @@ __global__ void __launch_bounds__(512) ypass_kernel(const cx<T>* __restrict__ tw
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* twy = buf + n2 * pitch;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(tw_n2 + i);
   cx<T>* Sp = S + ((long long)(lrhs * s_ncomp + c) * g.n3 + z) * g.plane_c;
   cx<T>* nyq = Sp + (long long)n2 * h;
+  // the column tile goes to shared memory by cp.async while the twiddle table loads
+  for (int e = tid; e < n2 * TY; e += nthr) {
+    const int y = e >> lg, t = e & (TY - 1);
+    cp_async_elem<sizeof(cx<T>)>(buf + y * pitch + t, Sp + (long long)y * h + kx0 + t);
+  }
+  for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(tw_n2 + i);
   if (prof != nullptr && tid == 0) {
     atomicAdd(prof, (unsigned long long)(2LL * n2 * TY * (long long)sizeof(cx<T>) +
                                          (kx0 == 0 ? (long long)n2 * (long long)sizeof(cx<T>) : 0)));
     atomicAdd(prof + 1, (unsigned long long)(n2 * TY));
   }
-  for (int e = tid; e < n2 * TY; e += nthr) {
-    const int y = e >> lg, t = e & (TY - 1);
-    cx<T> v = Sp[(long long)y * h + kx0 + t];
-    if (DIR > 0 && kx0 == 0 && t == 0) {  // pack A + i B
-      const cx<T> b = nyq[y];
-      v = mk<T>(v.re - b.im, v.im + b.re);
-    }
-    buf[y * pitch + t] = v;
-  }
+  cp_async_wait_all();
   __syncthreads();
+  if (DIR > 0 && kx0 == 0) {  // pack A + i B
+    for (int y = tid; y < n2; y += nthr) {
+      const cx<T> v = buf[y * pitch], b = nyq[y];
+      buf[y * pitch] = mk<T>(v.re - b.im, v.im + b.re);
+    }
+    __syncthreads();
+  }
   fft_pencils<T, DIR, EPT>(buf, ColAddr{pitch}, n2, TY, g.fd_ty, twy);
   if (DIR < 0 && kx0 == 0) {  // separate A (column 0) and B (Nyquist column)
     for (int ky = tid; 2 * ky <= n2; ky += nthr) {
