@@ -23,7 +23,8 @@ It shares no code with the CUDA path; the only common inputs are the seeded
 microstructures from ``paper_1712_05145_gb300.synthetic``, which callers pass in
 as plain arrays (this package imports none of the product package).
 
-Parity status per function is listed in each module header.  The order-2
-(paper alpha = 3) right-hand side builder is "parity unpinned" beyond linearity
-and symmetry checks, since the paper gives no value or closed form for it.
+Parity status per function is listed in each module header.  The paper prints no
+value for the higher-order tensors.  Their builders are pinned by symmetry and linearity
+checks, and by a laminate whose higher-order problems have closed solutions, to which the
+oracle's D_1 .. D_6 converge.
 """
