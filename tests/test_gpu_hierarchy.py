@@ -180,3 +180,31 @@ def test_order5_vanishes_for_centrosymmetric_cell():
     assert np.abs(H.effective(5)).max() < 1e-9 * np.abs(H.effective(4)).max()
     assert np.abs(H.effective(4)).max() > 1e-6
     H.close()
+
+
+def test_laminate_chain_converges_to_closed_solutions_on_gpu():
+    """The three-layer laminate of tests/test_oracle_laminate_hierarchy.py at 512 voxels across:
+    the GPU's D_1 .. D_6 along the chain E^11 Y2^o / o! match the closed ODE solutions to the
+    second-order discretisation error (about 1e-5 relative at this resolution)."""
+    from oracle.hierarchy import multisets
+    from paper_1712_05145_gb300 import hom
+    from tests.test_oracle_laminate_hierarchy import BOUNDS, LAME, MAX_ORDER, closed_chain
+    n = 512
+    phase = np.zeros((2, 2, n), dtype=np.uint8)
+    phase[:, :, int(BOUNDS[0] * n):int(BOUNDS[1] * n)] = 1
+    phase[:, :, int(BOUNDS[1] * n):] = 2
+    H = hom.Homogenization(synthetic.Microstructure(phase, LAME, 3.0, 2.0), precision=0)
+    for order in range(MAX_ORDER + 1):
+        info = H.solve(order, 1e-12)
+        assert all(i["status"] == 0 for i in info), order
+    ref = closed_chain(MAX_ORDER)
+    for o in range(1, MAX_ORDER + 1):
+        if o == 1:
+            col = 1                                   # load 3A + k, k = y2
+        elif o == 2:
+            col = 1                                   # load 6A + P, P = Mandel pair (2, 2)
+        else:
+            col = multisets(o).index((1,) * o)
+        got = H.effective(o)[5 if o % 2 == 1 else 0, col]
+        assert abs(got - ref[o]) < 5e-5 * abs(ref[o]), (o, got, ref[o])
+    H.close()
