@@ -85,15 +85,22 @@ typedef struct {
                               the default transforms all 6 unit loads per launch */
   void* cuda_stream;       /* cudaStream_t to run on; NULL = the handle's own stream */
   int32_t pass_mode;       /* x-y transforms: 0 = fused plane kernels when a plane fits one CTA,
-                              else split x and y passes; 1 = always fused (fails if a plane does
-                              not fit); 2 = always split */
+                              else (FP32 transforms) cluster plane passes, whose CTAs transpose
+                              the plane through distributed shared memory, or split x and y
+                              passes; 1 = always fused (fails if a plane does not fit); 2 = always
+                              split; 3 = always cluster for FP32 transforms (fails if no cluster
+                              shape fits), split for the FP64-accurate passes */
   int32_t autotune;        /* 1: before the first solve, time one operator application per
                               candidate launch shape (loads per launch, z-pass tile width) on
                               this grid and keep the fastest; 0 (default): fixed rules */
   int32_t polarization_variant; /* HOM_POLARIZATION: 0 = x <- T(x) (Eyre-Milton, Monchiet-Bonnet);
                               1 = x <- (x + T(x)) / 2 (the averaged, augmented-Lagrangian form,
                               which also converges where a phase modulus is 0) */
-  int32_t reserved[5];
+  int32_t z_mode;          /* z stage of the LS step: 0 = cluster z pass (six CTAs, one per Kelvin
+                              component, meeting in distributed shared memory for the Green
+                              contraction) where its tile fits, else the single-CTA z pass;
+                              1 = always the single-CTA z pass (three passes on deep grids) */
+  int32_t reserved[4];
 } hom_options;
 
 typedef struct {
@@ -190,7 +197,7 @@ HOM_API hom_status hom_ls_apply(hom_t h, int32_t nrhs, const double* eps_in, con
 
 /* Forward 3-D real-to-complex DFT, X[k] = sum_n x[n] exp(-2 pi i k.n/N) (unnormalised):
  * f: device double [nfield][N3][N2][N1]; fhat: device double complex (interleaved re, im)
- * [nfield][N3][N2][N1/2+1].  Computed in the handle's precision. */
+ * [nfield][N3][N2][N1/2+1]; 1 <= nfield <= 64.  Computed in the handle's precision. */
 HOM_API hom_status hom_fft_forward(hom_t h, int32_t nfield, const double* f, double* fhat);
 
 /* Inverse of hom_fft_forward without the 1/M factor: f[n] = sum_k X[k] exp(+2 pi i k.n/N)
@@ -233,12 +240,18 @@ HOM_API hom_status hom_profile_read(hom_t h, hom_kernel_stat* out);
  * does not own, or a loop that must not call cudaMalloc.  The paper has no counterpart; this is
  * the step of hom_ls_apply (FP64) with its scratch in a fixed device array of 16 MiB inside the
  * library, which every GPU that loads the library holds until the process exits.
- *  grid, phase    as hom_create, but phase must be a device pointer (not copied).
+ *  grid, phase    as hom_create (N3 = 1 is a two-dimensional cell), but phase must be a device
+ *                 pointer (not copied).  Its values must be < n_phase.  The call does not scan
+ *                 it: a value >= n_phase reads a zero row of the per-phase table, which keeps
+ *                 every access in bounds but gives a meaningless result for that voxel.
  *  n_phase, lame  as hom_create (lame is a host array); lambda0, mu0 the reference medium.
  *  eps_in, eps_out device double [nrhs][6][N3][N2][N1] Mandel (eps_in NULL = zero field);
- *                 E host double [nrhs][6] Mandel (NULL = zero); 1 <= nrhs <= 64.
- *  cuda_stream    cudaStream_t the work is queued on (NULL = legacy default stream); the call
- *                 returns once the work is queued, the result is ready when the stream is.
+ *                 eps_in == eps_out computes in place; other overlaps return HOM_ERR_ARG, and so
+ *                 do host pointers.  E host double [nrhs][6] Mandel (NULL = zero); 1 <= nrhs <= 64.
+ *  cuda_stream    cudaStream_t the work is queued on (NULL = legacy default stream).  The small
+ *                 tables (twiddles, per-phase eigenvalues, E) are copied from pageable host
+ *                 memory with cudaMemcpyAsync, so the call may block the calling thread until
+ *                 the stream reaches those copies; the result is ready when the stream is.
  * Limit: the spectrum of one load, 96 * N3 * N2 * (N1/2 + 1) bytes, plus small tables must fit
  * the 16 MiB (64^3 fits, 128 x 64 x 64 does not); larger grids return HOM_ERR_SIZE.
  * The first call on a device resolves the array's device address (cudaGetSymbolAddress); make
@@ -311,6 +324,14 @@ HOM_API int64_t hom_device_bytes(hom_t h);
  * tile width as log2 of its columns (-1: chosen per launch by the occupancy rule).  After an
  * autotuned solve these are the tuned values.  Pointers nullable. */
 HOM_API hom_status hom_launch_config(hom_t h, int32_t* loads_per_launch, int32_t* ztile_log2);
+
+/* x-y passes of the handle's FP32 transforms: *cluster_ctas = CTAs per plane of the cluster plane
+ * passes (hom_options.pass_mode), 0 when the fused plane kernels or the split x and y passes run. */
+HOM_API hom_status hom_plane_config(hom_t h, int32_t* cluster_ctas);
+
+/* z stage of the handle's iteration passes: *cluster = 1 for the cluster z pass (hom_options.z_mode),
+ * *tile_log2 its tile width as log2 of its columns (-1: the default rule).  Pointers nullable. */
+HOM_API hom_status hom_zpass_config(hom_t h, int32_t* cluster, int32_t* tile_log2);
 
 /* Kernels this library has launched in this process so far, over all handles, servers and the
  * allocation-free entry point (a host-side count of launches issued, not of launches finished). */

@@ -8,6 +8,8 @@ template <typename Tf>
 cudaError_t launch_mandel_to_kelvin(const double* in, Tf* out, long long M, int nf, cudaStream_t s);
 template <typename Tf>
 cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int nf, cudaStream_t s);
+// Mandel -> Kelvin of FP64 fields [nf][6][M] in place
+cudaError_t launch_mandel_to_kelvin_inplace(double* f, long long M, int nf, cudaStream_t s);
 // Kelvin -> Mandel of FP64 fields [nf][6][M] in place
 cudaError_t launch_kelvin_to_mandel_inplace(double* f, long long M, int nf, cudaStream_t s);
 // x[i] += d[i] for i < n

@@ -63,6 +63,20 @@ __global__ void kelvin_to_mandel_inplace_kernel(double* f, long long M, int nf) 
   }
 }
 
+// Mandel -> Kelvin of FP64 fields in place (input and output alias, as above)
+__global__ void mandel_to_kelvin_inplace_kernel(double* f, long long M, int nf) {
+  const long long total = (long long)nf * M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / M, v = i - q * M;
+    double* a = f + q * 6 * M + v;
+    const double m0 = a[0], m1 = a[M], m2 = a[2 * M];
+    a[0] = (m0 + m1 + m2) * R3;
+    a[M] = (m0 - m1) * R2;
+    a[2 * M] = (m0 + m1 - 2.0 * m2) * R6;
+  }
+}
+
 template <typename Ti, typename To>
 __global__ void convert_kernel(const Ti* __restrict__ in, To* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -92,6 +106,11 @@ cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int 
 cudaError_t launch_kelvin_to_mandel_inplace(double* f, long long M, int nf, cudaStream_t s) {
   count_launch();
   kelvin_to_mandel_inplace_kernel<<<grid_for(M * nf, 256), 256, 0, s>>>(f, M, nf);
+  return cudaGetLastError();
+}
+cudaError_t launch_mandel_to_kelvin_inplace(double* f, long long M, int nf, cudaStream_t s) {
+  count_launch();
+  mandel_to_kelvin_inplace_kernel<<<grid_for(M * nf, 256), 256, 0, s>>>(f, M, nf);
   return cudaGetLastError();
 }
 template <typename Ti, typename To>

@@ -14,12 +14,15 @@
 #include <cstring>
 #include <functional>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "aux.h"
 #include "equilibrium.h"
 #include "hierarchy.h"
+#include "plane_cluster.h"
 #include "polarization.h"
+#include "zcluster.h"
 #include "zsplit.h"
 #include "hom.h"
 #include "internal.h"
@@ -104,6 +107,9 @@ struct hom_ctx {
   int mblk = 64;
   void* d_work[4] = {nullptr, nullptr, nullptr, nullptr};
   int ztile_lg[2] = {-1, -1};  // z-pass tile width forced by the autotuner (FP32, FP64); -1: rule
+  int zc_lg[2] = {-1, -1};     // cluster z-pass tile width forced by the autotuner; -1: rule
+  bool zc_off[2] = {false, false};  // the autotuner found the single-CTA z pass faster
+  bool pc_off = false;         // the autotuner found the split x and y passes faster than the cluster ones
   bool tuned = false;
   void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t (the polarization scheme: eta)
   std::vector<double> kelvin;  // [n_phase][4] host copy of the material table: C - C0, C
@@ -191,7 +197,7 @@ hom_status work(hom_ctx* c, int i, size_t bytes, void** out) {
 
 // partial sums one load's reducing kernel publishes at most (one per CTA)
 size_t ncta_max(const hom_ctx* c) {
-  return 6 * (size_t)std::max(c->g.n3, c->g.split ? c->g.nrb : 0) + 64;
+  return 6 * (size_t)std::max(c->g.n3 * std::max(1, c->g.pc_Q), c->g.split ? c->g.nrb : 0) + 64;
 }
 
 // grows the per-load state, partial and load arrays to `n` loads
@@ -359,6 +365,10 @@ template <typename Tf, typename T>
 hom_status fwd_xy(hom_ctx* c, const FwdArgs<Tf, T>& fa, int n) {
   if (!c->g.split)
     return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_plane_fwd<Tf, T>(fa, n, c->stream); });
+  if constexpr (std::is_same<T, float>::value && std::is_same<Tf, float>::value) {
+    if (c->g.pc_Q > 0 && !c->pc_off)   // one cluster per plane, transposed in distributed shared memory
+      return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_plane_fwd_cluster(fa, n, c->stream); });
+  }
   CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_FWD), [&] { return launch_xpass_fwd<Tf, T>(fa, n, c->stream); }));
   const int yk = sizeof(T) == 8 ? HOM_KERNEL_YPASS_F64 : HOM_KERNEL_YPASS;
   unsigned long long* yp = c->prof_on ? c->d_prof + 2 * yk : nullptr;
@@ -372,6 +382,10 @@ template <typename Tf, typename T>
 hom_status inv_xy(hom_ctx* c, const InvArgs<Tf, T>& ia, int n) {
   if (!c->g.split)
     return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_plane_inv<Tf, T>(ia, n, c->stream); });
+  if constexpr (std::is_same<T, float>::value && std::is_same<Tf, float>::value) {
+    if (c->g.pc_Q > 0 && !c->pc_off)
+      return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_plane_inv_cluster(ia, n, c->stream); });
+  }
   const int yk = sizeof(T) == 8 ? HOM_KERNEL_YPASS_F64 : HOM_KERNEL_YPASS;
   unsigned long long* yp = c->prof_on ? c->d_prof + 2 * yk : nullptr;
   CKS(timed_launch(c, yk, [&] {
@@ -401,7 +415,13 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArg
     za.S = S;
     ia.S = S;
     CKS(fwd_xy<Tf1, T>(c, fa, n));
-    if (za.mode == Z_GAMMA && za.ncomp_in == 6 && ((size_t)1 << za.tc_log2) * sizeof(cx<T>) < 32) {
+    ZArgs<T> zc = za;
+    const int zi = sizeof(T) == 8 ? 1 : 0;
+    if (za.mode == Z_GAMMA && za.ncomp_in == 6 && za.ncomp_out == 6 && c->opt.z_mode == 0 && !c->zc_off[zi] &&
+        zcluster_tiling<T>(zc, c->zc_lg[zi])) {
+      // one pass: six CTAs per tile, the contraction in distributed shared memory
+      CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zcluster<T>(zc, n, c->stream); }));
+    } else if (za.mode == Z_GAMMA && za.ncomp_in == 6 && ((size_t)1 << za.tc_log2) * sizeof(cx<T>) < 32) {
       // deep grid: the fused z tiles would be narrower than a sector; split the z stage into
       // per-component z FFTs (one "load" per component, all loads of the chunk processed) and
       // a pointwise contraction
@@ -552,18 +572,28 @@ hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<i
 
 // Autotuner (hom_options.autotune): times one operator application per candidate launch shape
 // on this handle's grid and keeps the fastest per load.  The candidates are the loads per launch
-// (1, 2, 3, 4, 6, 8, 12, ... up to the spectrum scratch's capacity, at most 12) and the z-pass
-// tile widths that fit (2^0 .. 2^4 columns).  It tunes the passes of the iteration precision T.
+// (1, 2, 3, 4, 6, 8, 12, ... up to the spectrum scratch's capacity, at most 12) and the z stages
+// that fit: the single-CTA z pass with tiles of 2^0 .. 2^4 columns and the cluster z pass with
+// tiles of at least 32 bytes per z-plane.  It tunes the passes of the iteration precision T.
 template <typename T>
 hom_status autotune(hom_ctx* c) {
   const int nt = std::min(c->chunk, 12);
   std::vector<int> chunks;
   for (int k : {1, 2, 3, 4, 6, 8, 12})
     if (k <= nt) chunks.push_back(k);
-  std::vector<int> lgs;
+  // z-stage candidates: (0, lg) the single-CTA z pass with 2^lg columns, (1, lg) the cluster z pass
+  std::vector<std::pair<int, int>> zcand;
   for (int lg = 0; lg <= 4; ++lg)
-    if (zpass_tile_fits(c->g, sizeof(cx<T>), 6, lg)) lgs.push_back(lg);
-  if (lgs.empty()) return HOM_OK;
+    if (zpass_tile_fits(c->g, sizeof(cx<T>), 6, lg)) zcand.push_back({0, lg});
+  if (c->opt.z_mode == 0) {
+    for (int lg = 0; lg <= 6; ++lg) {
+      ZArgs<T> probe{};
+      probe.g = c->g;
+      if (((size_t)1 << lg) * sizeof(cx<T>) >= 32 && zcluster_tiling<T>(probe, lg) && probe.tc_log2 == lg)
+        zcand.push_back({1, lg});
+    }
+  }
+  if (zcand.empty()) return HOM_OK;
   const size_t fb = tbytes<T>(c, nt, 6);
   void *vin, *vout;
   CKS(work(c, 0, fb, &vin));
@@ -578,12 +608,21 @@ hom_status autotune(hom_ctx* c) {
   CKS(write_states(c, st));
   const int chunk0 = c->chunk, idx = sizeof(T) == 8 ? 1 : 0;
   cudaEvent_t e0 = pool_event(c), e1 = pool_event(c);
+  // x-y candidates: the cluster plane passes where the grid has them (FP32 transforms), and the split passes
+  std::vector<bool> pcand = {false};
+  if (std::is_same<T, float>::value && c->g.pc_Q > 0) pcand.push_back(true);
   double best = 1e300;
-  int best_chunk = chunk0, best_lg = -1;
+  int best_chunk = chunk0, best_lg = -1, best_kind = 0;
+  bool best_pc_off = false;
+  for (bool pc_off : pcand)
   for (int ck : chunks) {
-    for (int lg : lgs) {
+    for (const auto& zk : zcand) {
+      const int lg = zk.second;
+      c->pc_off = pc_off;
       c->chunk = ck;
-      c->ztile_lg[idx] = lg;
+      c->zc_off[idx] = (zk.first == 0);
+      if (zk.first == 0) c->ztile_lg[idx] = lg;
+      else c->zc_lg[idx] = lg;
       CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));  // warm-up
       CK(cudaEventRecord(e0, c->stream));
       for (int rep = 0; rep < 2; ++rep)
@@ -596,13 +635,23 @@ hom_status autotune(hom_ctx* c) {
         best = ms;
         best_chunk = ck;
         best_lg = lg;
+        best_kind = zk.first;
+        best_pc_off = pc_off;
       }
     }
   }
+  c->pc_off = best_pc_off;
   c->ev_pool.push_back(e0);
   c->ev_pool.push_back(e1);
   c->chunk = best_chunk;
-  c->ztile_lg[idx] = best_lg;
+  c->zc_off[idx] = (best_kind == 0);
+  if (best_kind == 0) {
+    c->ztile_lg[idx] = best_lg;
+    c->zc_lg[idx] = -1;
+  } else {
+    c->zc_lg[idx] = best_lg;
+    c->ztile_lg[idx] = -1;
+  }
   c->tuned = true;
   return HOM_OK;
 }
@@ -1426,6 +1475,26 @@ HOM_API hom_status hom_launch_config(hom_t c, int32_t* loads_per_launch, int32_t
   return HOM_OK;
 }
 
+HOM_API hom_status hom_plane_config(hom_t c, int32_t* cluster_ctas) {
+  if (!c) return HOM_ERR_ARG;
+  if (cluster_ctas) *cluster_ctas = (c->g.pc_Q > 0 && !c->pc_off) ? c->g.pc_Q : 0;
+  return HOM_OK;
+}
+
+HOM_API hom_status hom_zpass_config(hom_t c, int32_t* cluster, int32_t* tile_log2) {
+  if (!c) return HOM_ERR_ARG;
+  const int zi = c->fp32 ? 0 : 1;
+  ZArgs<float> p32{};
+  ZArgs<double> p64{};
+  p32.g = c->g;
+  p64.g = c->g;
+  bool on = c->opt.z_mode == 0 && !c->zc_off[zi];
+  if (on) on = c->fp32 ? zcluster_tiling<float>(p32, c->zc_lg[zi]) : zcluster_tiling<double>(p64, c->zc_lg[zi]);
+  if (cluster) *cluster = on ? 1 : 0;
+  if (tile_log2) *tile_log2 = on ? (c->fp32 ? p32.tc_log2 : p64.tc_log2) : c->ztile_lg[zi];
+  return HOM_OK;
+}
+
 HOM_API int64_t hom_launch_count(void) { return hom::launch_counter().load(std::memory_order_relaxed); }
 
 HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision) {
@@ -1517,7 +1586,8 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
       !z_length_supported(n3))
     return HOM_ERR_SIZE;
   const int pass_mode = opt ? opt->pass_mode : 0;
-  if (pass_mode < 0 || pass_mode > 2) return HOM_ERR_ARG;
+  if (pass_mode < 0 || pass_mode > 3) return HOM_ERR_ARG;
+  if (opt && (opt->z_mode < 0 || opt->z_mode > 1)) return HOM_ERR_ARG;
   if (pass_mode == 1 && (long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
 
   c = new hom_ctx();
@@ -1569,7 +1639,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   g.M = (long long)n1 * n2 * n3;
   g.plane_c = (long long)n2 * (g.h + 1);
   geo_finish(g);
-  g.split = (pass_mode == 2 || (pass_mode == 0 && (long long)g.n2 * g.h > 8192)) ? 1 : 0;
+  g.split = (pass_mode >= 2 || (pass_mode == 0 && (long long)g.n2 * g.h > 8192)) ? 1 : 0;
   const int nmax = std::max(n1, std::max(n2, n3));
   g.xs1 = 2.0 * M_PI * nmax / n1;
   g.xs2 = 2.0 * M_PI * nmax / n2;
@@ -1579,6 +1649,8 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     hom_destroy(c);
     return s;
   };
+  // FP32 transforms of split planes run as cluster plane passes (pass_mode 0 or 3)
+  if (g.split && pass_mode != 2 && c->fp32 && !plane_cluster_setup(g) && pass_mode == 3) return bail(HOM_ERR_SIZE);
 
   // phase array (host or device source) and its range check
   hom_status s;
@@ -1798,13 +1870,16 @@ hom_status fft_fwd_impl(hom_ctx* c, int nf, const double* f, double* fhat) {
   const size_t sb = sizeof(cx<T>) * (size_t)nf * c->g.n3 * c->g.plane_c;
   CKS(work(c, 2, sb, &vs));
   CK((launch_convert<double, T>(f, (T*)vin, (long long)nf * c->g.M, c->stream)));
+  // the nf fields are the components of one load for the x-y transforms (fused plane kernel or
+  // split x and y passes), and nf one-component loads for the z transforms
   auto fa = fwd_args<T, T>(c, FWD_COPY, nf, nf);
   fa.in = (const T*)vin;
   fa.S = (cx<T>*)vs;
-  CK((launch_plane_fwd<T, T>(fa, 1, c->stream)));
-  auto za = z_args<T>(c, Z_FWD, nf, nf);
+  CKS((fwd_xy<T, T>(c, fa, 1)));
+  auto za = z_args<T>(c, Z_FWD, 1, 1);
+  zpass_tiling<T>(za, -1);
   za.S = (cx<T>*)vs;
-  CK(launch_zpass<T>(za, 1, c->stream));
+  CK(launch_zpass<T>(za, nf, c->stream));
   CK(launch_spec_to_std<T>((const cx<T>*)vs, fhat, c->g, 1, nf, 0, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return HOM_OK;
@@ -1816,13 +1891,14 @@ hom_status fft_inv_impl(hom_ctx* c, int nf, const double* fhat, double* f) {
   const size_t sb = sizeof(cx<T>) * (size_t)nf * c->g.n3 * c->g.plane_c;
   CKS(work(c, 2, sb, &vs));
   CK(launch_spec_from_std<T>(fhat, (cx<T>*)vs, c->g, 1, nf, 0, c->stream));
-  auto za = z_args<T>(c, Z_INV, nf, nf);
+  auto za = z_args<T>(c, Z_INV, 1, 1);
+  zpass_tiling<T>(za, -1);
   za.S = (cx<T>*)vs;
-  CK(launch_zpass<T>(za, 1, c->stream));
+  CK(launch_zpass<T>(za, nf, c->stream));
   auto ia = inv_args<T, T>(c, INV_STORE, FIN_NONE, nf, nf, nf);
   ia.S = (const cx<T>*)vs;
   ia.out = (T*)vout;
-  CK((launch_plane_inv<T, T>(ia, 1, c->stream)));
+  CKS((inv_xy<T, T>(c, ia, 1)));
   CK((launch_convert<T, double>((const T*)vout, f, (long long)nf * c->g.M, c->stream)));
   CK(cudaStreamSynchronize(c->stream));
   return HOM_OK;
@@ -1846,11 +1922,11 @@ hom_status green_impl(hom_ctx* c, int nrhs, const double* th, double* eh) {
 extern "C" {
 
 HOM_API hom_status hom_fft_forward(hom_t c, int32_t nfield, const double* f, double* fhat) {
-  if (!c || !f || !fhat || nfield < 1 || nfield > 64 || (long long)nfield * c->g.n3 > 8192) return HOM_ERR_ARG;
+  if (!c || !f || !fhat || nfield < 1 || nfield > 64) return HOM_ERR_ARG;
   return c->fp32 ? fft_fwd_impl<float>(c, nfield, f, fhat) : fft_fwd_impl<double>(c, nfield, f, fhat);
 }
 HOM_API hom_status hom_fft_inverse(hom_t c, int32_t nfield, const double* fhat, double* f) {
-  if (!c || !f || !fhat || nfield < 1 || nfield > 64 || (long long)nfield * c->g.n3 > 8192) return HOM_ERR_ARG;
+  if (!c || !f || !fhat || nfield < 1 || nfield > 64) return HOM_ERR_ARG;
   return c->fp32 ? fft_inv_impl<float>(c, nfield, fhat, f) : fft_inv_impl<double>(c, nfield, fhat, f);
 }
 HOM_API hom_status hom_green_apply(hom_t c, int32_t nrhs, const double* tau_hat, double* eta_hat) {

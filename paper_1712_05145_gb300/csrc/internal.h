@@ -25,6 +25,10 @@ struct Geo {
   int ty_log2, thr_y;    // y pass: 2^ty_log2 consecutive columns per CTA, threads
   FastDiv fd_ty;         // division by 2^ty_log2
   double xs1, xs2, xs3;  // physical frequency per integer wave number: 2 pi Nmax / N_i
+  // cluster plane passes (split grids, FP32 transforms): pc_Q CTAs per plane (0: not used), each
+  // with pc_R = n2 / pc_Q rows and pc_Cb = h / pc_Q spectrum columns, pc_thr threads
+  int pc_Q, pc_R, pc_Cb, pc_thr;
+  FastDiv pc_fdR, pc_fdCb;  // division by pc_R and pc_Cb
 };
 
 // Per right-hand-side solver state, kept on the device (FP64).

@@ -35,6 +35,17 @@ hom_status noalloc_fail(hom_status s, const std::string& msg) {
   return s;
 }
 
+// true for memory the GPU addresses directly (device or managed); clears the error a host
+// pointer leaves behind
+bool device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Device address of the scratch array for the current device.  The first call on a device
@@ -84,20 +95,25 @@ HOM_API hom_status hom_ls_apply_noalloc(const int32_t grid[3], const uint8_t* ph
     return noalloc_fail(HOM_ERR_ARG, "hom_ls_apply_noalloc: degenerate reference medium");
   const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
   if (n1 < 4 || (n1 & 1) || !fft_length_supported(n1 / 2) || !fft_length_supported(n2) ||
-      !fft_length_supported(n3) || (long long)(n1 / 2) * n2 > 8192)
+      !z_length_supported(n3) || (long long)(n1 / 2) * n2 > 8192)
     return noalloc_fail(HOM_ERR_SIZE, "hom_ls_apply_noalloc: grid axis not supported");
   const size_t need = noalloc_scratch_need(n1, n2, n3, nrhs);
   if (need > kNoallocScratchBytes)
     return noalloc_fail(HOM_ERR_SIZE, "hom_ls_apply_noalloc: grid needs " + std::to_string(need) +
                                           " bytes of scratch, more than the fixed " +
                                           std::to_string(kNoallocScratchBytes));
-  {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, phase) != cudaSuccess ||
-        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-      cudaGetLastError();
-      return noalloc_fail(HOM_ERR_ARG, "hom_ls_apply_noalloc: phase must be a device pointer");
-    }
+  // every array the kernels touch must be device memory: a host pointer would fault on the GPU
+  if (!device_pointer(phase))
+    return noalloc_fail(HOM_ERR_ARG, "hom_ls_apply_noalloc: phase must be a device pointer");
+  if (!device_pointer(eps_out) || (eps_in != nullptr && !device_pointer(eps_in)))
+    return noalloc_fail(HOM_ERR_ARG, "hom_ls_apply_noalloc: eps_in and eps_out must be device pointers");
+  const size_t field_bytes = sizeof(double) * 6 * (size_t)n1 * n2 * n3 * nrhs;
+  const bool in_place = (eps_in == eps_out);
+  if (eps_in != nullptr && !in_place) {
+    const char* a = reinterpret_cast<const char*>(eps_in);
+    const char* b = reinterpret_cast<const char*>(eps_out);
+    if (a < b + field_bytes && b < a + field_bytes)
+      return noalloc_fail(HOM_ERR_ARG, "hom_ls_apply_noalloc: eps_in and eps_out overlap without being equal");
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   unsigned char* base = nullptr;
@@ -176,10 +192,12 @@ HOM_API hom_status hom_ls_apply_noalloc(const int32_t grid[3], const uint8_t* ph
   NA_CK(cudaMemcpyAsync(dE, hE.data(), sizeof(double) * hE.size(), cudaMemcpyHostToDevice, s));
 
   // Kelvin components of the input into the output buffer; the step then runs in place there
-  if (eps_in) {
+  if (in_place) {
+    NA_CK(launch_mandel_to_kelvin_inplace(eps_out, g.M, nrhs, s));
+  } else if (eps_in) {
     NA_CK(launch_mandel_to_kelvin<double>(eps_in, eps_out, g.M, nrhs, s));
   } else {
-    NA_CK(cudaMemsetAsync(eps_out, 0, sizeof(double) * 6 * (size_t)g.M * nrhs, s));
+    NA_CK(cudaMemsetAsync(eps_out, 0, field_bytes, s));
   }
 
   FwdArgs<double, double> fa{};
@@ -189,7 +207,10 @@ HOM_API hom_status hom_ls_apply_noalloc(const int32_t grid[3], const uint8_t* ph
   fa.in_ncomp = 6;
   fa.phase = phase;
   fa.mat = mat;
-  fa.n_phase = n_phase;
+  // the kernels stage a table of n_phase rows in shared memory and index it by the raw phase
+  // byte, which this entry point does not scan; the table holds all 256 rows (zero past the
+  // caller's n_phase), so every byte value stays inside it
+  fa.n_phase = 256;
   fa.in = eps_out;
   fa.E = dE;
   fa.S = S;

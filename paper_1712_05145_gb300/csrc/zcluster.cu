@@ -1,0 +1,165 @@
+// Cluster z pass of the Lippmann-Schwinger step (Sec. 2 of arXiv:1712.05145, Algorithm 1: the
+// transform along z, eta_hat = -Gamma0_hat(xi) : tau_hat with eta_hat(0) = 0, the inverse
+// transform along z).
+//
+// A tile is 2^lg consecutive spectrum columns (flat index f of the x-y half-spectrum plane) over
+// all N3 z-planes.  Six CTAs form a thread-block cluster; CTA c (its rank) holds component c of
+// the tile in its shared memory and runs that component's z FFTs.  The contraction needs all six
+// components at a frequency, so after a cluster barrier each CTA contracts one sixth of the
+// tile's frequencies, reading and writing the six components in the other CTAs' shared memory
+// (distributed shared memory).  A second cluster barrier precedes the inverse z FFTs.
+//
+// Compared with one CTA holding all six components of a narrower tile, each CTA reads and writes
+// runs of 2^lg complex values per z-plane (128 bytes at 16 FP32 columns) instead of 16-32 bytes,
+// and at N3 = 512 the z stage stays one pass over the spectrum instead of three.
+#include <cooperative_groups.h>
+
+#include "ls_common.cuh"
+#include "spectral.cuh"
+#include "zcluster.h"
+
+namespace cg = cooperative_groups;
+
+namespace hom {
+
+constexpr int kZcComps = 6;            // CTAs per cluster: one per Kelvin component
+constexpr int kZcMaxElems = kEPT * 512;
+constexpr size_t kZcMaxSmem = 80 * 1024;
+// two 512-thread CTAs per SM in FP32 (64 registers); the 16-byte types keep more registers
+template <typename T> struct ZcCfg { static constexpr int kMinBlocks = 1; };
+template <> struct ZcCfg<float> { static constexpr int kMinBlocks = 2; };
+
+template <typename T, int EPT>
+__global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>::kMinBlocks) zcluster_kernel(const ZArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const Geo& g = a.g;
+  const int comp = (int)cl.block_rank();
+  const int tile = blockIdx.x / kZcComps, lrhs = blockIdx.y, rhs = a.rhs0 + lrhs;
+  // the six CTAs of a cluster share the load, so they leave together (before any barrier)
+  if (a.st != nullptr && a.st[rhs].active == 0) return;
+  const int lg = a.tc_log2, TC = 1 << lg, n3 = g.n3;
+  const int per = n3 * TC;   // elements of this CTA's tile
+  const long long f0 = (long long)tile * TC;
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);   // [n3][TC]
+  cx<T>* twz = buf + per;                             // exp(-2 pi i t / n3)
+  const int tid = threadIdx.x, nthr = blockDim.x;
+
+  cx<T>* Sc = a.S + (long long)(lrhs * kZcComps + comp) * n3 * g.plane_c;
+  for (int e = tid; e < per; e += nthr) {
+    const int tc = e & (TC - 1), n = e >> lg;
+    const long long f = f0 + tc;
+    if (f < g.plane_c) cp_async_elem<sizeof(cx<T>)>(buf + e, Sc + (long long)n * g.plane_c + f);
+    else buf[e] = mk<T>(0, 0);
+  }
+  for (int i = tid; i < n3; i += nthr) twz[i] = ldg_cx(a.tw_n3 + i);
+  const long long cols = (g.plane_c - f0 < TC) ? g.plane_c - f0 : TC;
+  if (a.prof != nullptr && tid == 0) {
+    atomicAdd(a.prof, (unsigned long long)(2LL * n3 * cols * (long long)sizeof(cx<T>)));
+    if (comp == 0) atomicAdd(a.prof + 1, (unsigned long long)(n3 * cols));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  fft_pencils<T, -1, EPT>(buf, ColAddr{TC}, n3, TC, a.fd_in, twz);
+  cl.sync();   // every component of the tile is transformed along z
+
+  {
+    cx<T>* part[kZcComps];
+#pragma unroll
+    for (int r = 0; r < kZcComps; ++r) part[r] = cl.map_shared_rank(buf, r);
+    const T c1 = (T)(1.0 / (2.0 * a.mu0));
+    const T c2h = (T)((a.lam0 + a.mu0) / (2.0 * a.mu0 * (a.lam0 + 2.0 * a.mu0)));
+    const T scale = (T)a.scale;
+    const long long nmain = (long long)g.n2 * g.h;
+    const int share = (per + kZcComps - 1) / kZcComps;
+    const int q0 = comp * share, q1 = (q0 + share < per) ? q0 + share : per;
+    for (int q = q0 + tid; q < q1; q += nthr) {
+      const int tc = q & (TC - 1), n = q >> lg;
+      const long long f = f0 + tc;
+      if (f >= g.plane_c) continue;
+      int kx, ky;
+      if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
+      else { ky = (int)(f - nmain); kx = g.h; }
+      // discrete wave vector: Nyquist components taken as 0
+      const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
+      const T x2 = (T)(wave(ky, g.n2) * g.xs2);
+      const T x3 = (T)(wave(n, n3) * g.xs3);
+      cx<T> k[6], tt[6], w1, w2, w3;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) k[i] = part[i][q];
+      kelvin_to_tensor<T>(k, tt);
+      tensor_dot_xi<T>(tt, x1, x2, x3, w1, w2, w3);
+      green_from_w<T>(k, w1, w2, w3, x1, x2, x3, c1, c2h, scale);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) part[i][q] = k[i];
+    }
+  }
+  cl.sync();   // every frequency of the tile is contracted; no CTA touches another's memory after this
+
+  fft_pencils<T, +1, EPT>(buf, ColAddr{TC}, n3, TC, a.fd_in, twz);
+  for (int e = tid; e < per; e += nthr) {
+    const int tc = e & (TC - 1), n = e >> lg;
+    const long long f = f0 + tc;
+    if (f < g.plane_c) Sc[(long long)n * g.plane_c + f] = buf[e];
+  }
+}
+
+static size_t zcluster_smem(const Geo& g, size_t elem, int lg) {
+  return ((size_t)g.n3 * ((size_t)1 << lg) + g.n3) * elem;
+}
+
+bool zcluster_tile_fits(const Geo& g, size_t elem, int lg) {
+  return lg >= 0 && lg <= 6 && (long long)g.n3 * (1LL << lg) <= kZcMaxElems &&
+         zcluster_smem(g, elem, lg) <= kZcMaxSmem;
+}
+
+// Default width: grow the tile while it stays within about 256 threads, or while its runs along
+// the flat index are shorter than 128 bytes (one full memory transaction per z-plane).
+template <typename T>
+bool zcluster_tiling(ZArgs<T>& a, int force_lg) {
+  const size_t elem = sizeof(cx<T>);
+  if (a.g.n3 < 16) return false;   // shallow grids: the single-CTA z pass has more work per CTA
+  int best = -1;
+  if (force_lg >= 0 && zcluster_tile_fits(a.g, elem, force_lg)) {
+    best = force_lg;
+  } else {
+    for (int lg = 0; lg <= 6; ++lg) {
+      if (!zcluster_tile_fits(a.g, elem, lg)) break;
+      if (best < 0 || (long long)a.g.n3 * (1LL << lg) <= 4096 || ((size_t)1 << best) * elem < 128) best = lg;
+    }
+  }
+  if (best < 0) return false;
+  a.tc_log2 = best;
+  const long long tc = 1LL << best;
+  a.ntiles = (int)((a.g.plane_c + tc - 1) / tc);
+  const long long e = (long long)a.g.n3 * tc;
+  int thr = (int)((e + kEPT - 1) / kEPT);
+  thr = ((thr + 31) / 32) * 32;
+  a.nthr = thr < 64 ? 64 : thr;
+  a.fd_in = make_fastdiv((unsigned)tc);
+  return true;
+}
+template bool zcluster_tiling<float>(ZArgs<float>&, int);
+template bool zcluster_tiling<double>(ZArgs<double>&, int);
+template bool zcluster_tiling<df64>(ZArgs<df64>&, int);
+
+template <typename T>
+cudaError_t launch_zcluster(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
+  const long long e = (long long)a.g.n3 * (1LL << a.tc_log2);
+  if (a.mode != Z_GAMMA || a.ncomp_in != 6 || a.ncomp_out != 6 || !zcluster_tile_fits(a.g, sizeof(cx<T>), a.tc_log2) ||
+      e > (long long)kEPT * a.nthr || a.nthr > 512 || nrhs < 1 || (long long)a.ntiles * kZcComps > 0x7fffffffLL)
+    return cudaErrorInvalidValue;
+  const size_t smem = zcluster_smem(a.g, sizeof(cx<T>), a.tc_log2);
+  auto k = zcluster_kernel<T, kEPT>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  dim3 grid((unsigned)(a.ntiles * kZcComps), (unsigned)nrhs);
+  count_launch();
+  k<<<grid, a.nthr, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zcluster<float>(const ZArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_zcluster<double>(const ZArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_zcluster<df64>(const ZArgs<df64>&, int, cudaStream_t);
+
+}  // namespace hom

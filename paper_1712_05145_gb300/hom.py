@@ -46,7 +46,9 @@ EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "
             "hom_ls_apply", "hom_equilibrium_error", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
             "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
             "hom_server_create", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
-            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_launch_count", "hom_last_error",
+            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_zpass_config", "hom_plane_config",
+            "hom_launch_count",
+            "hom_last_error",
             "hom_status_string", "hom_destroy"]
 
 
@@ -55,7 +57,8 @@ class hom_options(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
                 ("spectrum_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("pass_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("polarization_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("polarization_variant", ctypes.c_int32), ("z_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -160,6 +163,10 @@ def load_library(path=None):
     lib.hom_device_bytes.restype = I64
     lib.hom_launch_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.hom_launch_config.restype = ctypes.c_int
+    lib.hom_plane_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32)]
+    lib.hom_plane_config.restype = ctypes.c_int
+    lib.hom_zpass_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.hom_zpass_config.restype = ctypes.c_int
     lib.hom_launch_count.argtypes = []
     lib.hom_launch_count.restype = I64
     lib.hom_last_error.argtypes = [V]
@@ -373,6 +380,20 @@ def hom_launch_config(h):
     return a.value, b.value
 
 
+def hom_plane_config(h):
+    """CTAs per plane of the cluster plane passes of a handle's FP32 transforms (0: not used)."""
+    a = ctypes.c_int32()
+    _check(h, load_library().hom_plane_config(h, ctypes.byref(a)))
+    return a.value
+
+
+def hom_zpass_config(h):
+    """(1 if the cluster z pass runs else 0, its tile log2 width or -1) of a handle's iteration passes."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(h, load_library().hom_zpass_config(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def hom_launch_count():
     """Kernels the library has launched in this process (host-side count)."""
     return int(load_library().hom_launch_count())
@@ -395,7 +416,7 @@ class Homogenization:
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
                  max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,
-                 pass_mode=0, autotune=0, polarization_variant=0):
+                 pass_mode=0, autotune=0, polarization_variant=0, z_mode=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
         self.M = n1 * n2 * n3
@@ -411,6 +432,7 @@ class Homogenization:
         opt.pass_mode = pass_mode
         opt.autotune = autotune
         opt.polarization_variant = polarization_variant
+        opt.z_mode = z_mode
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
                             ms.mu0 if mu0 is None else mu0, opt)
         self.nloads = {}

@@ -68,9 +68,10 @@ def test_config_c1_laminate32_closed_form(precision, scheme):
     H.close()
 
 
-@pytest.mark.parametrize("pass_mode", [0, 2])
+@pytest.mark.parametrize("pass_mode", [0, 2, 3])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_random_spheres_32_cg_vs_oracle(precision, pass_mode):
+    """Fused plane kernels (0), split x and y passes (2), cluster plane passes (3, FP32)."""
     from paper_1712_05145_gb300 import hom
     ms = synthetic.random_spheres((32, 32, 32), seed=3)
     pb = Problem(ms.phase, ms.lame, ms.lam0, ms.mu0)
@@ -172,7 +173,12 @@ def test_autotuned_launch_shape_gives_identical_results(precision):
         info = H.solve(0, 1e-8)
         assert all(i["status"] == 0 for i in info)
         chunk, lg = hom.hom_launch_config(H.h)
-        assert chunk >= 1 and (lg == -1) == (tune == 0)
+        cluster, zlg = hom.hom_zpass_config(H.h)
+        assert chunk >= 1
+        if tune:   # the tuner reports its choice: a single-CTA tile width or a cluster tile width
+            assert (cluster == 0 and lg >= 0) or (cluster == 1 and zlg >= 0)
+        else:
+            assert lg == -1 and cluster == 1
         out.append((H.effective(0), H.field(0, 2), [i["iterations"] for i in info]))
         H.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
