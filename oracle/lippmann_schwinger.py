@@ -94,9 +94,13 @@ class Problem:
             tau = tau + iso_apply(self.lam, self.mu, ebig)
         return tau
 
+    def green(self, tau_hat):
+        """eta_hat = -Gamma0_hat : tau_hat with eta_hat(0) = 0 (the Green operator of Sec. 2)."""
+        return green_apply(tau_hat, self.grid, self.lam0, self.mu0)
+
     def minus_gamma_conv(self, tau):
         """-Gamma0 * tau as the Fourier series of Eq. strain_solution (real field)."""
-        eta_hat = green_apply(fourier.forward(tau), self.grid, self.lam0, self.mu0)
+        eta_hat = self.green(fourier.forward(tau))
         return fourier.inverse(eta_hat).real
 
     def ls_step(self, eps, E):
@@ -112,7 +116,7 @@ class Problem:
         """A eps = (Id + Gamma0 * (C - C0)) : eps, via Algorithm 1's loop body."""
         tau = iso_apply(self.lam - self.lam0, self.mu - self.mu0, eps)     # polarization
         tau_hat = fourier.forward(tau)                                      # transform
-        eta_hat = green_apply(tau_hat, self.grid, self.lam0, self.mu0)     # -Gamma0_hat, eta(0)=0
+        eta_hat = self.green(tau_hat)                                       # -Gamma0_hat, eta(0)=0
         eta = fourier.inverse(eta_hat).real                                 # inverse transform
         return eps - eta                                                    # eps_n - eta_n
 
