@@ -61,6 +61,7 @@ typedef enum {
 enum { HOM_FP64 = 0, HOM_FP32_REFINE = 1 };
 enum { HOM_BASIC = 0, HOM_CG = 1, HOM_BICGSTAB = 2, HOM_POLARIZATION = 3 };
 enum { HOM_FIELD_STRAIN = 0, HOM_FIELD_DISPLACEMENT = 1, HOM_FIELD_STRESS = 2 };
+enum { HOM_GREEN_SPECTRAL = 0, HOM_GREEN_ROTATED = 1 };
 
 typedef struct {
   int32_t precision;       /* HOM_FP64: FP64 fields and FFTs.  HOM_FP32_REFINE: FP32 fields and
@@ -100,7 +101,22 @@ typedef struct {
                               component, meeting in distributed shared memory for the Green
                               contraction) where its tile fits, else the single-CTA z pass;
                               1 = always the single-CTA z pass (three passes on deep grids) */
-  int32_t reserved[4];
+  int32_t green_operator;  /* HOM_GREEN_SPECTRAL (0): Gamma0_hat of Sec. 2 at the discrete wave
+                              vector (Nyquist components 0).  HOM_GREEN_ROTATED (1): the Green
+                              operator of the rotated finite-difference discretisation (corner
+                              displacements, voxel-centre strains, derivatives averaged over the four
+                              voxel edges along an axis; one of the discrete operators of the FFT
+                              schemes Sec. 1 cites): Gamma0_hat evaluated at q_j = sin(xi_j h/2)
+                              prod_{l != j} cos(xi_l h/2), zero where q = 0.  Order 0 only; the
+                              equilibrium diagnostic stays spectral and is not offered with it. */
+  int32_t n_rve;           /* RVE slots of one grid held by the handle (1..10, 0 = 1).  With more than
+                              one, every LS launch carries the loads of all slots: load r belongs to
+                              slot r / 6, and each slot has its own phase array, per-phase table and
+                              reference medium (hom_set_rve).  Such a handle solves order 0 for the
+                              6 unit loads of each slot (hom_solve with loads = NULL, n_loads =
+                              6 x slots, 0 = all) with CG, BiCGSTAB or the Basic Scheme; hom_effective
+                              returns the 6 x (6 x slots) mean stresses, one 6 x 6 block per slot. */
+  int32_t reserved[2];
 } hom_options;
 
 typedef struct {
@@ -161,6 +177,14 @@ HOM_API hom_status hom_solve(hom_t h, int32_t order, int32_t n_loads, const doub
  *           stress of the paper's alpha = 2);
  *  order o >= 2: 6 x (its loads), column = <C : eps_{o+1} + p_{o+1}>. */
 HOM_API hom_status hom_effective(hom_t h, int32_t order, double* out);
+
+/* Replaces the microstructure of RVE slot `slot` (0 .. n_rve - 1) of a handle without any device
+ * allocation: phase (host or device, copied; every value < n_phase), n_phase, lame and the
+ * reference medium as hom_create.  The grid and options stay.  Solved orders of the handle are
+ * discarded.  Waits for the handle's stream.  This lets a server keep handles of the grids it
+ * sees resident and refill them per request (the paper has no counterpart). */
+HOM_API hom_status hom_set_rve(hom_t h, int32_t slot, const uint8_t* phase, int32_t n_phase, const double* lame,
+                               double lambda0, double mu0);
 
 /* Copies one corrector field of a solved order to dst (double):
  *  HOM_FIELD_STRAIN       6 x [N3][N2][N1] Mandel strain fluctuation eps;
@@ -272,12 +296,19 @@ HOM_API const char* hom_noalloc_last_error(void);
 HOM_API int64_t hom_estimate_bytes(const int32_t grid[3], int32_t order, int32_t precision);
 
 /* ---- request server: continuous batching of RVE solves (no counterpart in the paper) ----
- * Requests are copied on submission and queued.  max_active worker threads, each with its own
- * CUDA stream, admit queued requests first-fit against a device-memory budget (estimate above)
- * as soon as a worker and enough memory are free; the kernels of admitted requests overlap on
- * the device.  Each request runs hom_create / hom_solve (order 0, then order 1 if asked) /
- * hom_effective / hom_destroy with default options of its precision and scheme, so its result
- * is the same as when solved alone. */
+ * Requests are copied on submission and queued.  max_active worker threads admit queued requests
+ * first-fit against a device-memory budget as soon as a worker is free:
+ *  - an admitted order-0 request takes with it up to max_batch - 1 further queued order-0 requests
+ *    of the same grid, precision, scheme and tolerance; they are solved in one handle with one RVE
+ *    slot each (hom_options.n_rve), so every launch of the solve carries all of their loads;
+ *  - handles stay resident per (grid, precision, scheme, order, slots) and are refilled with the
+ *    next requests by hom_set_rve, so admission allocates no device memory once a kind has been
+ *    seen; idle handles of other kinds are destroyed, least recently used first, when a new kind
+ *    does not fit the budget;
+ *  - every handle runs on its own stream, so different grids' launches overlap on the device.
+ * Each load's arithmetic is that of its RVE solved alone (per-load solver state and refinement
+ * decisions, per-slot tables and reference media), so a request's result does not depend on what
+ * it was batched or overlapped with. */
 typedef struct hom_server_ctx* hom_server_t;
 
 typedef struct {
@@ -304,15 +335,23 @@ typedef struct {
   char message[160];       /* hom_last_error text of a failed request, "" on success */
 } hom_result;
 
-/* budget_bytes <= 0: 85 % of the free device memory at creation.  1 <= max_active <= 64. */
+/* budget_bytes <= 0: 85 % of the free device memory at creation.  1 <= max_active <= 64;
+ * 1 <= max_batch <= 10 RVEs per batched handle (1: every request alone in its handle).
+ * hom_server_create is hom_server_create_batched with max_batch = 8. */
+HOM_API hom_status hom_server_create_batched(int64_t budget_bytes, int32_t max_active, int32_t max_batch,
+                                             hom_server_t* out);
 HOM_API hom_status hom_server_create(int64_t budget_bytes, int32_t max_active, hom_server_t* out);
+/* Batches run, requests run in them, and handles created so far (each pointer nullable). */
+HOM_API hom_status hom_server_counters(hom_server_t s, int64_t* batches, int64_t* requests_run,
+                                       int64_t* handles_created);
 /* Queues a request; *id identifies it.  HOM_ERR_NOMEM if it can never fit the budget. */
 HOM_API hom_status hom_server_submit(hom_server_t s, const hom_request* req, int64_t* id);
 /* Copies the result if the request is done (out->done = 1), else sets out->done = 0. */
 HOM_API hom_status hom_server_poll(hom_server_t s, int64_t id, hom_result* out);
 /* Blocks until the request is done, then copies its result. */
 HOM_API hom_status hom_server_wait(hom_server_t s, int64_t id, hom_result* out);
-/* Queue length, running requests and the estimated bytes they hold (each pointer nullable). */
+/* Queue length, running requests and the device bytes the server's handles hold or have reserved
+ * (each pointer nullable). */
 HOM_API hom_status hom_server_stats(hom_server_t s, int64_t* queued, int64_t* running, int64_t* bytes_in_use);
 /* Waits for every queued and running request, then releases the server. */
 HOM_API void hom_server_destroy(hom_server_t s);

@@ -24,10 +24,11 @@ cudaError_t launch_spec_from_std(const double* in, cx<T>* S, const Geo& g, int n
 template <typename T>
 cudaError_t launch_spec_to_std(const cx<T>* S, double* out, const Geo& g, int nf, int ncomp, int basis,
                                cudaStream_t s);
-// out[rhs * ncomp + c] = mean over voxels of w(phase, c) * (f[rhs][c] + shift[rhs][c])
+// out[rhs * ncomp + c] = mean over voxels of w(phase, c) * (f[rhs][c] + shift[rhs][c]); with
+// rve_loads > 0, load rhs reads the phase array and table of RVE rhs / rve_loads
 template <typename Tf>
 cudaError_t launch_weighted_mean(const Tf* f, int ncomp, int nrhs, const double* shift, const uint8_t* phase,
                                  const double* mat, int wsel, long long M, double* part, int nblk, double* out,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int rve_loads = 0);
 
 }  // namespace hom

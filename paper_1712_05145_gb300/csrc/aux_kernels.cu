@@ -254,10 +254,15 @@ cudaError_t launch_spec_to_std(const cx<T>* S, double* out, const Geo& g, int nf
 template <typename Tf>
 __global__ void mean_partial_kernel(const Tf* __restrict__ f, int ncomp, const double* __restrict__ shift,
                                     const uint8_t* __restrict__ phase, const double* __restrict__ mat,
-                                    int wsel, long long M, double* __restrict__ part) {
+                                    int wsel, long long M, int rve_loads, double* __restrict__ part) {
   __shared__ double sh[64];
   const int c = blockIdx.y, rhs = blockIdx.z, nb = gridDim.x;
   const Tf* src = f + ((long long)rhs * ncomp + c) * M;
+  if (rve_loads > 0) {   // several RVEs in one handle: this load's phase array and table
+    const int rve = rhs / rve_loads;
+    phase += (long long)rve * M;
+    mat += (long long)rve * 4 * 256;
+  }
   const double sft = shift ? shift[rhs * 6 + c] : 0.0;
   const int col = (wsel < 0) ? -1 : wsel + (c == 0 ? 0 : 1);
   double acc = 0.0;
@@ -283,10 +288,10 @@ __global__ void mean_final_kernel(const double* __restrict__ part, int nb, long 
 template <typename Tf>
 cudaError_t launch_weighted_mean(const Tf* f, int ncomp, int nrhs, const double* shift, const uint8_t* phase,
                                  const double* mat, int wsel, long long M, double* part, int nblk, double* out,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, int rve_loads) {
   dim3 g1(nblk, ncomp, nrhs);
   count_launch();
-  mean_partial_kernel<Tf><<<g1, 256, 0, s>>>(f, ncomp, shift, phase, mat, wsel, M, part);
+  mean_partial_kernel<Tf><<<g1, 256, 0, s>>>(f, ncomp, shift, phase, mat, wsel, M, rve_loads, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   count_launch();
@@ -307,8 +312,9 @@ template cudaError_t launch_spec_from_std<double>(const double*, cx<double>*, co
 template cudaError_t launch_spec_to_std<float>(const cx<float>*, double*, const Geo&, int, int, int, cudaStream_t);
 template cudaError_t launch_spec_to_std<double>(const cx<double>*, double*, const Geo&, int, int, int, cudaStream_t);
 template cudaError_t launch_weighted_mean<float>(const float*, int, int, const double*, const uint8_t*, const double*,
-                                                 int, long long, double*, int, double*, cudaStream_t);
+                                                 int, long long, double*, int, double*, cudaStream_t, int);
 template cudaError_t launch_weighted_mean<double>(const double*, int, int, const double*, const uint8_t*,
-                                                  const double*, int, long long, double*, int, double*, cudaStream_t);
+                                                  const double*, int, long long, double*, int, double*, cudaStream_t,
+                                                  int);
 
 }  // namespace hom

@@ -65,6 +65,7 @@ struct OrderData {
   bool solved = false;
   bool disp_ok = false;   // displacement correctors computed for the current strains
   int nloads = 0;
+  int cap = 0;            // loads the buffers below hold (>= nloads)
   void* eps = nullptr;    // Tf [nloads][6][M] Kelvin strain fluctuation
   void* disp = nullptr;   // Tf [nloads][3][M] displacement corrector
   void* pf = nullptr;     // Tf [nloads][6][M] Kelvin polarization p_alpha (orders >= 1)
@@ -115,6 +116,11 @@ struct hom_ctx {
   std::vector<double> kelvin;  // [n_phase][4] host copy of the material table: C - C0, C
   double* d_polar64 = nullptr; // [n_phase][4] polarization-scheme table (c0 w, w), built on first use
   float* d_polar32 = nullptr;
+  double* d_gtab = nullptr;    // rotated finite-difference Green operator: sin, cos of pi j / N per axis
+  int n_rve = 1;               // RVE slots of one grid (hom_options.n_rve)
+  int rve_loads = 0;           // n_rve > 1: loads per slot (6, the unit loads); 0 with one RVE
+  double* d_c0 = nullptr;      // n_rve > 1: [slot][4] (lambda0, mu0, 3 lambda0 + 2 mu0, 2 mu0)
+  std::vector<double> c0_host; // n_rve > 1: host copy of d_c0
   size_t bicg_bytes = 0;
   size_t work_bytes[4] = {0, 0, 0, 0};
   OrderData ord[kMaxOrder + 1];
@@ -250,6 +256,8 @@ FwdArgs<Tf, T> fwd_args(hom_ctx* c, int mode, int ncomp, int in_ncomp) {
   a.n_phase = c->nphase;
   a.c0h = (T)(3.0 * c->lam0 + 2.0 * c->mu0);
   a.c0d = (T)(2.0 * c->mu0);
+  a.rve_loads = c->rve_loads;
+  a.c0 = c->rve_loads > 0 ? c->d_c0 : nullptr;
   a.part = part_fwd(c);
   a.cnt = cnt_fwd(c);
   a.prof = c->prof_on ? c->d_prof + 2 * (HOM_KERNEL_PLANE_FWD + (sizeof(T) == 8 ? 3 : 0)) : nullptr;
@@ -267,9 +275,13 @@ ZArgs<T> z_args(hom_ctx* c, int mode, int nin, int nout) {
   a.ncomp_out = nout;
   a.lam0 = c->lam0;
   a.mu0 = c->mu0;
+  a.rve_loads = c->rve_loads;
+  a.c0 = c->rve_loads > 0 ? c->d_c0 : nullptr;
   a.scale = 1.0 / (double)c->g.M;
   a.prof = c->prof_on ? c->d_prof + 2 * (HOM_KERNEL_ZPASS + (sizeof(T) == 8 ? 3 : 0)) : nullptr;
   a.tw_n3 = tw<T>(c, 3);
+  a.green = c->opt.green_operator;
+  a.gtab = c->d_gtab;
   zpass_tiling<T>(a, c->ztile_lg[sizeof(T) == 8 ? 1 : 0]);
   return a;
 }
@@ -284,6 +296,8 @@ InvArgs<Tf, T> inv_args(hom_ctx* c, int mode, int fin, int ncomp, int out_ncomp,
   a.s_ncomp = s_ncomp;
   a.c0h = (T)(3.0 * c->lam0 + 2.0 * c->mu0);
   a.c0d = (T)(2.0 * c->mu0);
+  a.rve_loads = c->rve_loads;
+  a.c0 = c->rve_loads > 0 ? c->d_c0 : nullptr;
   a.out_scale = (T)1;
   a.part = part_inv(c);
   a.cnt = cnt_inv(c);
@@ -512,8 +526,10 @@ hom_status equilibrium_t(hom_ctx* c, int n, const double* epsK, double* d_part, 
 // (about 1e-7 of ||x||).  x32 and p32 are FP32 scratch of n loads.
 hom_status project_compatible_fp32(hom_ctx* c, int n, double* x64, float* x32, float* p32,
                                    const std::vector<int>* act) {
-  const long long cnt = (long long)n * 6 * c->g.M;
-  CK((launch_convert<double, float>(x64, x32, cnt, c->stream)));
+  // only the loads of `act` are touched: the conversion and the correction run load by load
+  const long long per = 6 * c->g.M;
+  for (int i = 0; i < n; ++i)
+    if (!act || (*act)[i]) CK((launch_convert<double, float>(x64 + i * per, x32 + i * per, per, c->stream)));
   auto fa = fwd_args<float, float>(c, FWD_C0, 6, 6);
   fa.in = x32;
   fa.st = c->d_st;
@@ -524,7 +540,8 @@ hom_status project_compatible_fp32(hom_ctx* c, int n, double* x64, float* x32, f
   ia.out_scale = -1.0f;
   ia.st = c->d_st;
   CKS((ls_pass<float, float, float>(c, n, fa, za, ia, act)));
-  CK(launch_add_difference(p32, x32, x64, cnt, c->stream));
+  for (int i = 0; i < n; ++i)
+    if (!act || (*act)[i]) CK(launch_add_difference(p32 + i * per, x32 + i * per, x64 + i * per, per, c->stream));
   return HOM_OK;
 }
 
@@ -1048,17 +1065,30 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
           CKS(write_states(c, st));
           if (!rest) break;
         }
-        // after the loose first sweep an FP32 projection suffices: its rounding (~1e-7 of ||x||) is
-        // far below the tolerance and the literal check at the end sees whatever is left
-        bool loose = true;
-        for (int i = 0; i < n; ++i)
-          if (act[i] && (refine[i] > 0 || st[i].tol <= tol)) loose = false;
-        if (loose) {
-          CKS(project_compatible_fp32(c, n, x64, reinterpret_cast<float*>(d), reinterpret_cast<float*>(r), &act));
-          CK(cudaMemsetAsync(d, 0, fb, c->stream));   // d was scratch; the next sweep starts from 0
-        } else {
-          CKS(project_compatible(c, n, x64, &act));
+        // after a load's loose first sweep an FP32 projection suffices: its rounding (~1e-7 of ||x||)
+        // is far below the tolerance and the literal check at the end sees whatever is left; later
+        // projections run at FP64 accuracy.  The choice is made per load, so a load's arithmetic does
+        // not depend on the other loads solved with it.
+        std::vector<int> loose(n, 0), tight(n, 0);
+        bool any_loose = false, any_tight = false;
+        for (int i = 0; i < n; ++i) {
+          if (!act[i]) continue;
+          if (refine[i] > 0 || st[i].tol <= tol) tight[i] = 1, any_tight = true;
+          else loose[i] = 1, any_loose = true;
         }
+        if (any_loose) {
+          for (int i = 0; i < n; ++i) st[i].active = loose[i];
+          CKS(write_states(c, st));
+          CKS(project_compatible_fp32(c, n, x64, reinterpret_cast<float*>(d), reinterpret_cast<float*>(r), &loose));
+          CK(cudaMemsetAsync(d, 0, fb, c->stream));   // d was scratch; the next sweep starts from 0
+        }
+        if (any_tight) {
+          for (int i = 0; i < n; ++i) st[i].active = tight[i];
+          CKS(write_states(c, st));
+          CKS(project_compatible(c, n, x64, &tight));
+        }
+        for (int i = 0; i < n; ++i) st[i].active = act[i];
+        CKS(write_states(c, st));
       }
       CKS(residual_sweep<Tf>(c, n, dE, b64, x64, r, FIN_RESID, &act));
       CKS(read_states(c, n, st));
@@ -1108,17 +1138,24 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
   return worst;
 }
 
+// The fields of an order for nloads loads.  The buffers only grow, so a handle that solves batches
+// of varying size (a resident serving handle) allocates once for its largest one.
 hom_status alloc_order(hom_ctx* c, int order, int nloads, bool with_p) {
   OrderData& o = c->ord[order];
-  if (o.eps && o.nloads == nloads) return HOM_OK;
-  if (o.eps) dfree(c, o.eps, tbytes<double>(c, o.nloads, 6));
-  if (o.disp) dfree(c, o.disp, tbytes<double>(c, o.nloads, 3));
-  if (o.pf) dfree(c, o.pf, tbytes<double>(c, o.nloads, 6));
+  if (o.eps && o.cap >= nloads && (!with_p || o.pf)) {
+    o.nloads = nloads;
+    return HOM_OK;
+  }
+  const int cap = std::max(nloads, o.cap);
+  if (o.eps) dfree(c, o.eps, tbytes<double>(c, o.cap, 6));
+  if (o.disp) dfree(c, o.disp, tbytes<double>(c, o.cap, 3));
+  if (o.pf) dfree(c, o.pf, tbytes<double>(c, o.cap, 6));
   o.eps = o.disp = o.pf = nullptr;
   o.nloads = nloads;
-  CKS(dalloc(c, &o.eps, tbytes<double>(c, nloads, 6)));
-  CKS(dalloc(c, &o.disp, tbytes<double>(c, nloads, 3)));
-  if (with_p) CKS(dalloc(c, &o.pf, tbytes<double>(c, nloads, 6)));
+  o.cap = cap;
+  CKS(dalloc(c, &o.eps, tbytes<double>(c, cap, 6)));
+  CKS(dalloc(c, &o.disp, tbytes<double>(c, cap, 3)));
+  if (with_p) CKS(dalloc(c, &o.pf, tbytes<double>(c, cap, 6)));
   return HOM_OK;
 }
 
@@ -1131,7 +1168,8 @@ hom_status mean_stress(hom_ctx* c, int order, std::vector<double>& eff) {
   if (order == 0)
     CK(cudaMemcpyAsync(c->d_E, o.loadsK.data(), sizeof(double) * 6 * n, cudaMemcpyHostToDevice, c->stream));
   CK(launch_weighted_mean<double>(reinterpret_cast<const double*>(o.eps), 6, n, order == 0 ? c->d_E : nullptr,
-                                  c->d_phase, c->d_mat64, 2, c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream));
+                                  c->d_phase, c->d_mat64, 2, c->g.M, c->d_mpart, c->mblk, c->d_mout, c->stream,
+                                  c->rve_loads));
   CK(cudaMemcpyAsync(hk.data(), c->d_mout, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
   if (order > 0) {
     CK(launch_weighted_mean<double>(reinterpret_cast<const double*>(o.pf), 6, n, nullptr, c->d_phase, c->d_mat64,
@@ -1310,7 +1348,7 @@ hom_status solve_order0(hom_ctx* c, int n, const double* loads, double tol, hom_
   for (int i = 0; i < n; ++i) {
     double m[6] = {0, 0, 0, 0, 0, 0};
     if (loads) for (int j = 0; j < 6; ++j) m[j] = loads[i * 6 + j];
-    else m[i] = 1.0;
+    else m[i % 6] = 1.0;   // the unit loads (of each RVE slot in turn)
     mandel_to_kelvin6(m, &o.loadsK[i * 6]);
   }
   CKS(ensure_cap(c, n));
@@ -1574,6 +1612,58 @@ HOM_API void hom_destroy(hom_t h) {
   delete h;
 }
 
+// Copies one RVE into slot `slot` of the handle: the phase array (host or device source, every
+// value < n_phase), the per-phase Kelvin eigenvalues of C - C0 and C in FP64, FP32 and
+// double-float, and the reference medium.  Synchronous on the handle's stream.
+hom_status set_rve_data(hom_ctx* c, int slot, const uint8_t* phase, int n_phase, const double* lame, double lambda0,
+                        double mu0) {
+  const Geo& g = c->g;
+  std::vector<uint8_t> hph((size_t)g.M);
+  if (is_device_ptr(phase)) {
+    CK(cudaMemcpy(hph.data(), phase, (size_t)g.M, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(hph.data(), phase, (size_t)g.M);
+  }
+  for (size_t i = 0; i < hph.size(); ++i)
+    if (hph[i] >= n_phase) return fail(c, HOM_ERR_ARG, "phase value %d >= n_phase %d", (int)hph[i], n_phase);
+  // per-phase Kelvin eigenvalues: C - C0 (3 dK, 2 dmu), C (3K, 2mu)
+  std::vector<double> m64(4 * 256, 0.0);
+  std::vector<float> m32(4 * 256, 0.0f);
+  for (int i = 0; i < n_phase; ++i) {
+    const double l = lame[2 * i], m = lame[2 * i + 1];
+    if (!std::isfinite(l) || !std::isfinite(m)) return fail(c, HOM_ERR_ARG, "non-finite Lame parameter");
+    m64[4 * i + 0] = 3.0 * (l - lambda0) + 2.0 * (m - mu0);
+    m64[4 * i + 1] = 2.0 * (m - mu0);
+    m64[4 * i + 2] = 3.0 * l + 2.0 * m;
+    m64[4 * i + 3] = 2.0 * m;
+    for (int j = 0; j < 4; ++j) m32[4 * i + j] = (float)m64[4 * i + j];
+  }
+  std::vector<df64> mdf(4 * 256, df64(0.0f, 0.0f));
+  for (int i = 0; i < 4 * 256; ++i) mdf[i] = df64(m64[i]);
+  const size_t t = (size_t)slot * 4 * 256;
+  CK(cudaMemcpyAsync(c->d_phase + (size_t)slot * g.M, hph.data(), (size_t)g.M, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_mat64 + t, m64.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_mat32 + t, m32.data(), sizeof(float) * 4 * 256, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_mat_df + t, mdf.data(), sizeof(df64) * 4 * 256, cudaMemcpyHostToDevice, c->stream));
+  if (c->n_rve > 1) {
+    // the C0 weights are computed here as the one-RVE path computes its scalar c0h, c0d, so that a
+    // slot's arithmetic is that of a handle holding its RVE alone
+    double* w = &c->c0_host[4 * slot];
+    w[0] = lambda0;
+    w[1] = mu0;
+    w[2] = 3.0 * lambda0 + 2.0 * mu0;
+    w[3] = 2.0 * mu0;
+    CK(cudaMemcpyAsync(c->d_c0 + 4 * slot, w, sizeof(double) * 4, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    c->nphase = n_phase;
+    c->lam0 = lambda0;
+    c->mu0 = mu0;
+    c->kelvin.assign(m64.begin(), m64.begin() + 4 * n_phase);
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
 HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32_t n_phase, const double* lame,
                               double lambda0, double mu0, const hom_options* opt, hom_t* out) {
   hom_ctx* c = nullptr;
@@ -1588,6 +1678,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   const int pass_mode = opt ? opt->pass_mode : 0;
   if (pass_mode < 0 || pass_mode > 3) return HOM_ERR_ARG;
   if (opt && (opt->z_mode < 0 || opt->z_mode > 1)) return HOM_ERR_ARG;
+  if (opt && opt->green_operator != HOM_GREEN_SPECTRAL && opt->green_operator != HOM_GREEN_ROTATED) return HOM_ERR_ARG;
   if (pass_mode == 1 && (long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
 
   c = new hom_ctx();
@@ -1618,6 +1709,12 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   c->nphase = n_phase;
   c->lam0 = lambda0;
   c->mu0 = mu0;
+  c->n_rve = c->opt.n_rve < 1 ? 1 : c->opt.n_rve;
+  if (c->n_rve > kMaxRve || (c->n_rve > 1 && c->opt.scheme == HOM_POLARIZATION)) {
+    delete c;
+    return HOM_ERR_ARG;
+  }
+  c->rve_loads = c->n_rve > 1 ? 6 : 0;
   cudaGetDevice(&c->device);
   if (c->opt.cuda_stream) {
     c->stream = reinterpret_cast<cudaStream_t>(c->opt.cuda_stream);
@@ -1652,40 +1749,19 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   // FP32 transforms of split planes run as cluster plane passes (pass_mode 0 or 3)
   if (g.split && pass_mode != 2 && c->fp32 && !plane_cluster_setup(g) && pass_mode == 3) return bail(HOM_ERR_SIZE);
 
-  // phase array (host or device source) and its range check
+  // phase arrays and per-phase tables of every RVE slot (all filled with the given RVE)
   hom_status s;
-  if ((s = dalloc(c, (void**)&c->d_phase, (size_t)g.M)) != HOM_OK) return bail(s);
-  std::vector<uint8_t> hph((size_t)g.M);
-  if (is_device_ptr(phase)) {
-    if (cudaMemcpy(hph.data(), phase, (size_t)g.M, cudaMemcpyDeviceToHost) != cudaSuccess) return bail(HOM_ERR_CUDA);
-  } else {
-    std::memcpy(hph.data(), phase, (size_t)g.M);
+  if (c->n_rve > 1) c->nphase = 256;   // slots may differ in their phase counts; tables are padded
+  if ((s = dalloc(c, (void**)&c->d_phase, (size_t)g.M * c->n_rve)) != HOM_OK) return bail(s);
+  if ((s = dalloc(c, (void**)&c->d_mat64, sizeof(double) * 4 * 256 * c->n_rve)) != HOM_OK) return bail(s);
+  if ((s = dalloc(c, (void**)&c->d_mat32, sizeof(float) * 4 * 256 * c->n_rve)) != HOM_OK) return bail(s);
+  if ((s = dalloc(c, (void**)&c->d_mat_df, sizeof(df64) * 4 * 256 * c->n_rve)) != HOM_OK) return bail(s);
+  if (c->n_rve > 1) {
+    if ((s = dalloc(c, (void**)&c->d_c0, sizeof(double) * 4 * c->n_rve)) != HOM_OK) return bail(s);
+    c->c0_host.assign(4 * c->n_rve, 0.0);
   }
-  for (size_t i = 0; i < hph.size(); ++i)
-    if (hph[i] >= n_phase) return bail(HOM_ERR_ARG);
-  if (cudaMemcpy(c->d_phase, hph.data(), (size_t)g.M, cudaMemcpyHostToDevice) != cudaSuccess) return bail(HOM_ERR_CUDA);
-
-  // per-phase Kelvin eigenvalues: C - C0 (3 dK, 2 dmu), C (3K, 2mu)
-  std::vector<double> m64(4 * 256, 0.0);
-  std::vector<float> m32(4 * 256, 0.0f);
-  for (int i = 0; i < n_phase; ++i) {
-    const double l = lame[2 * i], m = lame[2 * i + 1];
-    if (!std::isfinite(l) || !std::isfinite(m)) return bail(HOM_ERR_ARG);
-    m64[4 * i + 0] = 3.0 * (l - lambda0) + 2.0 * (m - mu0);
-    m64[4 * i + 1] = 2.0 * (m - mu0);
-    m64[4 * i + 2] = 3.0 * l + 2.0 * m;
-    m64[4 * i + 3] = 2.0 * m;
-    for (int j = 0; j < 4; ++j) m32[4 * i + j] = (float)m64[4 * i + j];
-  }
-  c->kelvin.assign(m64.begin(), m64.begin() + 4 * n_phase);
-  if ((s = dalloc(c, (void**)&c->d_mat64, sizeof(double) * 4 * 256)) != HOM_OK) return bail(s);
-  if ((s = dalloc(c, (void**)&c->d_mat32, sizeof(float) * 4 * 256)) != HOM_OK) return bail(s);
-  cudaMemcpy(c->d_mat64, m64.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice);
-  cudaMemcpy(c->d_mat32, m32.data(), sizeof(float) * 4 * 256, cudaMemcpyHostToDevice);
-  std::vector<df64> mdf(4 * 256, df64(0.0f, 0.0f));
-  for (int i = 0; i < 4 * 256; ++i) mdf[i] = df64(m64[i]);
-  if ((s = dalloc(c, (void**)&c->d_mat_df, sizeof(df64) * 4 * 256)) != HOM_OK) return bail(s);
-  cudaMemcpy(c->d_mat_df, mdf.data(), sizeof(df64) * 4 * 256, cudaMemcpyHostToDevice);
+  for (int slot = 0; slot < c->n_rve; ++slot)
+    if ((s = set_rve_data(c, slot, phase, n_phase, lame, lambda0, mu0)) != HOM_OK) return bail(s);
 
   // twiddle tables exp(-2 pi i t / L) for L = h, n1, n2, n3 (host libm, FP64)
   std::vector<cx<double>> t64;
@@ -1710,6 +1786,21 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   }
   if ((s = dalloc(c, (void**)&c->d_tw_df, sizeof(cx<df64>) * tdf.size())) != HOM_OK) return bail(s);
   cudaMemcpy(c->d_tw_df, tdf.data(), sizeof(cx<df64>) * tdf.size(), cudaMemcpyHostToDevice);
+
+  // the rotated finite-difference operator's per-axis table: sin(pi j / N), cos(pi j / N) by DFT index
+  // (j <= N1/2 on the half-spectrum axis), cos exactly 0 at j = N/2
+  if (c->opt.green_operator == HOM_GREEN_ROTATED) {
+    std::vector<double> gt;
+    auto axis = [&](int n, int count) {
+      for (int j = 0; j < count; ++j) gt.push_back(std::sin(M_PI * j / n));
+      for (int j = 0; j < count; ++j) gt.push_back(2 * j == n ? 0.0 : std::cos(M_PI * j / n));
+    };
+    axis(n1, g.h + 1);
+    axis(n2, n2);
+    axis(n3, n3);
+    if ((s = dalloc(c, (void**)&c->d_gtab, sizeof(double) * gt.size())) != HOM_OK) return bail(s);
+    cudaMemcpy(c->d_gtab, gt.data(), sizeof(double) * gt.size(), cudaMemcpyHostToDevice);
+  }
 
   // spectrum scratch
   const size_t elem = c->fp32 ? sizeof(cx<float>) : sizeof(cx<double>);
@@ -1742,11 +1833,20 @@ HOM_API hom_status hom_solve(hom_t c, int32_t order, int32_t n_loads, const doub
     hom_status t = c->fp32 ? autotune<float>(c) : autotune<double>(c);
     if (t != HOM_OK) return t;
   }
+  if (c->n_rve > 1) {
+    // several RVE slots: the 6 unit loads of the first n_loads / 6 slots (all slots for 0)
+    if (order != 0 || loads) return fail(c, HOM_ERR_ARG, "a handle with several RVEs solves order 0, unit loads only");
+    const int n = n_loads > 0 ? n_loads : 6 * c->n_rve;
+    if (n % 6 != 0 || n > 6 * c->n_rve) return fail(c, HOM_ERR_ARG, "n_loads must be 6 x (RVE slots to solve)");
+    return c->fp32 ? solve_order0<float>(c, n, nullptr, tol, info) : solve_order0<double>(c, n, nullptr, tol, info);
+  }
   if (order == 0) {
     int n = loads ? n_loads : 6;
     if (n < 1 || n > 64) return fail(c, HOM_ERR_ARG, "n_loads must be in 1..64");
     return c->fp32 ? solve_order0<float>(c, n, loads, tol, info) : solve_order0<double>(c, n, loads, tol, info);
   }
+  if (c->opt.green_operator != HOM_GREEN_SPECTRAL)
+    return fail(c, HOM_ERR_ARG, "the higher-order problems are built with the spectral Green operator only");
   if (order >= 2 && loads) return fail(c, HOM_ERR_ARG, "orders >= 2 take only their unit loads (loads = NULL)");
   int n = loads_of_order(order);
   if (order == 1 && loads) {
@@ -1756,6 +1856,34 @@ HOM_API hom_status hom_solve(hom_t c, int32_t order, int32_t n_loads, const doub
   c->ord[order].solved = false;
   return c->fp32 ? solve_higher<float>(c, order, n, loads, tol, info)
                  : solve_higher<double>(c, order, n, loads, tol, info);
+}
+
+HOM_API hom_status hom_set_rve(hom_t c, int32_t slot, const uint8_t* phase, int32_t n_phase, const double* lame,
+                               double lambda0, double mu0) {
+  if (!c || !phase || !lame) return HOM_ERR_ARG;
+  if (slot < 0 || slot >= c->n_rve) return fail(c, HOM_ERR_ARG, "slot out of range");
+  if (n_phase < 1 || n_phase > 256) return fail(c, HOM_ERR_ARG, "n_phase must be in 1..256");
+  if (!(mu0 != 0.0) || !(lambda0 + 2.0 * mu0 != 0.0) || !std::isfinite(lambda0) || !std::isfinite(mu0))
+    return fail(c, HOM_ERR_ARG, "degenerate reference medium");
+  if (c->opt.scheme == HOM_POLARIZATION) {
+    bool ok = (mu0 > 0.0) && (3.0 * lambda0 + 2.0 * mu0 > 0.0);
+    for (int i = 0; i < n_phase && ok; ++i)
+      ok = (2.0 * lame[2 * i + 1] >= 0.0) && (3.0 * lame[2 * i] + 2.0 * lame[2 * i + 1] >= 0.0);
+    if (!ok) return fail(c, HOM_ERR_ARG, "the polarization scheme needs non-negative moduli");
+  }
+  CK(cudaStreamSynchronize(c->stream));   // no pass of the previous RVE still reads the tables
+  CKS(set_rve_data(c, slot, phase, n_phase, lame, lambda0, mu0));
+  // the polarization tables and every solved order belonged to the previous microstructure
+  dfree(c, c->d_polar64, sizeof(double) * 4 * 256);
+  dfree(c, c->d_polar32, sizeof(float) * 4 * 256);
+  c->d_polar64 = nullptr;
+  c->d_polar32 = nullptr;
+  for (int k = 0; k <= kMaxOrder; ++k) {
+    c->ord[k].solved = false;
+    c->ord[k].disp_ok = false;
+    c->ord[k].eff.clear();
+  }
+  return HOM_OK;
 }
 
 HOM_API hom_status hom_effective(hom_t c, int32_t order, double* out) {
@@ -1776,6 +1904,8 @@ HOM_API hom_status hom_get_field(hom_t c, int32_t order, int32_t load, int32_t k
   if (load < 0 || load >= o.nloads) return fail(c, HOM_ERR_ARG, "load out of range");
   if (kind != HOM_FIELD_STRAIN && kind != HOM_FIELD_DISPLACEMENT && kind != HOM_FIELD_STRESS)
     return fail(c, HOM_ERR_ARG, "unknown field kind");
+  if (kind == HOM_FIELD_DISPLACEMENT && c->opt.green_operator != HOM_GREEN_SPECTRAL)
+    return fail(c, HOM_ERR_ARG, "displacements are recovered with the spectral operator only");
   const int nc = (kind == HOM_FIELD_DISPLACEMENT) ? 3 : 6;
   const size_t nbytes = sizeof(double) * nc * (size_t)c->g.M;
   double* d = dst;
@@ -1793,6 +1923,9 @@ HOM_API hom_status hom_get_field(hom_t c, int32_t order, int32_t load, int32_t k
 
 HOM_API hom_status hom_equilibrium_error(hom_t c, int32_t nrhs, const double* eps, const double* E, double* out) {
   if (!c || !out) return HOM_ERR_ARG;
+  if (c->n_rve > 1) return fail(c, HOM_ERR_ARG, "the equilibrium diagnostic takes a handle with one RVE");
+  if (c->opt.green_operator != HOM_GREEN_SPECTRAL)
+    return fail(c, HOM_ERR_ARG, "the equilibrium diagnostic measures the spectral divergence only");
   const OrderData& o = c->ord[0];
   if (!eps) {
     if (!o.eps || o.eff.empty()) return fail(c, HOM_ERR_ORDER, "order 0 has not been solved");

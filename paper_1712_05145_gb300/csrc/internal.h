@@ -7,6 +7,8 @@
 
 namespace hom {
 
+constexpr int kMaxRve = 10;   // RVE slots of one handle (6 unit loads each, at most 64 loads per solve)
+
 // Geometry of one voxel grid and its spectrum layout.
 //  fields   [rhs][comp][n3][n2][n1]            real, x fastest
 //  spectrum [rhs][comp][n3][plane_c]           complex; one x-y plane holds the
@@ -76,6 +78,9 @@ struct FwdArgs {
   const T* mat;                // [n_phase][4] Kelvin eigenvalues: C-C0 (h, dev), C (h, dev)
   T c0h, c0d;                  // FWD_C0: C0 Kelvin eigenvalues 3 lam0 + 2 mu0, 2 mu0
   int n_phase;
+  int rve_loads;               // > 0: the handle holds several RVEs, rve_loads consecutive loads each;
+                               // load r reads phase + (r / rve_loads) M and its RVE's 256-row table
+  const double* c0;            // rve_loads > 0: [rve][4] (lambda0, mu0, 3 lambda0 + 2 mu0, 2 mu0) per RVE
   const Tf* in;                // FWD_TAU: strain (nullable); FWD_COPY: field
   const double* E;             // FWD_TAU: [rhs][6] Kelvin macroscopic strain (nullable)
   const Tf* r;                 // FWD_CG
@@ -105,7 +110,11 @@ struct ZArgs {
   int rhs0;
   const RhsState* st;
   double lam0, mu0;
+  int rve_loads;         // > 0: loads per RVE of a several-RVE handle, whose reference media are
+  const double* c0;      //   c0[rve][4] = (lambda0, mu0, 3 lambda0 + 2 mu0, 2 mu0) in place of lam0, mu0
   double scale;          // factor applied with the spectral operator (1/M after a forward FFT)
+  int green;             // 0: spectral wave vector; 1: rotated finite-difference vector q (gtab)
+  const double* gtab;    // green == 1: sin, cos of pi j / N per axis (see wave_vector)
   unsigned long long* prof;
   const cx<T>* tw_n3;
 };
@@ -118,6 +127,8 @@ struct InvArgs {
   const cx<T>* S;
   int rhs0;
   T c0h, c0d;            // C0 Kelvin eigenvalues: 3 lam0 + 2 mu0, 2 mu0
+  int rve_loads;         // > 0: loads per RVE of a several-RVE handle, whose reference media are
+  const double* c0;      //   c0[rve][4] = (lambda0, mu0, 3 lambda0 + 2 mu0, 2 mu0) in place of c0h, c0d
   T out_scale;           // INV_STORE: out = out_scale * eta (+ b)
   Tf* out;               // INV_STORE
   const double* b;       // INV_STORE: added right-hand-side field, FP64 (nullable)

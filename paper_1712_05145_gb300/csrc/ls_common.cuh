@@ -51,6 +51,24 @@ constexpr int kStallItersNearFloor = 25;
 constexpr double kNearFloor = 1e-5;
 
 // ---------------------------------------------------------------------------------
+// several RVEs of one grid in one handle: load r belongs to RVE r / rve_loads (rve_loads > 0)
+__device__ __forceinline__ int rve_of(int rhs, int rve_loads) { return rve_loads > 0 ? rhs / rve_loads : 0; }
+constexpr int kRveTable = 4 * 256;   // per-phase table entries of one RVE
+
+// Kelvin eigenvalues of C0 (3 lam0 + 2 mu0, 2 mu0) of an RVE: from c0[rve] = (lam0, mu0, 3 lam0 + 2 mu0,
+// 2 mu0) when given (computed on the host, like h and d), else (h, d)
+template <typename T>
+__device__ __forceinline__ void c0_weights(const double* c0, int rve, T h, T d, T& ch, T& cd) {
+  if (c0 != nullptr) {
+    ch = (T)c0[4 * rve + 2];
+    cd = (T)c0[4 * rve + 3];
+  } else {
+    ch = h;
+    cd = d;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // small helpers
 template <typename Tf> struct Pair;
 template <> struct Pair<float> { using V = float2; };

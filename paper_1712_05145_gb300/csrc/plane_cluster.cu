@@ -66,10 +66,12 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
+  const int rve = rve_of(rhs, a.rve_loads);
   if (a.mode != FWD_COPY && a.mode != FWD_C0) {
+    const T* mat = a.mat + (long long)rve * kRveTable;
     for (int i = tid; i < a.n_phase; i += nthr) {
-      tab[i] = a.mat[i * 4 + (c == 0 ? 0 : 1)];                 // C - C0 eigenvalue
-      tab[a.n_phase + i] = a.mat[i * 4 + (c == 0 ? 2 : 3)];     // C eigenvalue
+      tab[i] = mat[i * 4 + (c == 0 ? 0 : 1)];                 // C - C0 eigenvalue
+      tab[a.n_phase + i] = mat[i * 4 + (c == 0 ? 2 : 3)];     // C eigenvalue
     }
   }
   __syncthreads();
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)blk_sz);
   }
-  const uint8_t* php = a.phase + (long long)z * plane_sz + (long long)y0 * n1;
+  const uint8_t* php = a.phase + (long long)rve * g.M + (long long)z * plane_sz + (long long)y0 * n1;
   T acc = (T)0;
   const int total = R * h;   // complex elements of this CTA's rows (flat index e = row * h + col)
 
@@ -140,7 +142,9 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
       }
     }
   } else {  // FWD_COPY, FWD_C0
-    const T w = (a.mode == FWD_C0) ? (c == 0 ? a.c0h : a.c0d) : (T)1;
+    T ch, cd;
+    c0_weights<T>(a.c0, rve, a.c0h, a.c0d, ch, cd);
+    const T w = (a.mode == FWD_C0) ? (c == 0 ? ch : cd) : (T)1;
     for (int e = tid; e < total; e += nthr) {
       const int row = (int)g.fd_h.div((unsigned)e), col = e - row * h;
       const long long o = (long long)row * n1 + 2 * col;
@@ -253,7 +257,8 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_inv_cluster_kernel(con
   const int z = blockIdx.x / Q, c = blockIdx.y, lrhs = blockIdx.z, rhs = a.rhs0 + lrhs;
   if (a.st != nullptr && a.st[rhs].active == 0) return;
   const int n1 = g.n1, n2 = g.n2, h = g.h, P = g.P;
-  const T c0h = a.c0h, c0d = a.c0d;
+  T c0h, c0d;
+  c0_weights<T>(a.c0, rve_of(rhs, a.rve_loads), a.c0h, a.c0d, c0h, c0d);
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* nyq = buf + R * P;
   cx<T>* twh = nyq + n2;

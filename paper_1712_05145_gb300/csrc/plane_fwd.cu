@@ -45,10 +45,12 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i < n2; i += nthr) twy[i] = ldg_cx(a.tw_n2 + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
+  const int rve = rve_of(rhs, a.rve_loads);
   if (a.mode != FWD_COPY && a.mode != FWD_C0) {
+    const T* mat = a.mat + (long long)rve * kRveTable;
     for (int i = tid; i < a.n_phase; i += nthr) {
-      tab[i] = a.mat[i * 4 + (c == 0 ? 0 : 1)];                 // C - C0 eigenvalue
-      tab[a.n_phase + i] = a.mat[i * 4 + (c == 0 ? 2 : 3)];     // C eigenvalue
+      tab[i] = mat[i * 4 + (c == 0 ? 0 : 1)];                 // C - C0 eigenvalue
+      tab[a.n_phase + i] = mat[i * 4 + (c == 0 ? 2 : 3)];     // C eigenvalue
     }
   }
   __syncthreads();
@@ -63,7 +65,7 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
     atomicAdd(a.prof, (unsigned long long)b);
     atomicAdd(a.prof + 1, (unsigned long long)plane_sz);
   }
-  const uint8_t* php = a.phase + (long long)z * plane_sz;
+  const uint8_t* php = a.phase + (long long)rve * g.M + (long long)z * plane_sz;
   T acc = (T)0;
 
   if (a.mode == FWD_TAU || a.mode == FWD_STRESS) {
@@ -120,7 +122,9 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
       }
     }
   } else {  // FWD_COPY, FWD_C0
-    const T w = (a.mode == FWD_C0) ? (c == 0 ? a.c0h : a.c0d) : (T)1;
+    T ch, cd;
+    c0_weights<T>(a.c0, rve, a.c0h, a.c0d, ch, cd);
+    const T w = (a.mode == FWD_C0) ? (c == 0 ? ch : cd) : (T)1;
     #pragma unroll 4
     for (int row = warp; row < n2; row += nwarp) {
       for (int c2 = lane; c2 < h; c2 += 32) {

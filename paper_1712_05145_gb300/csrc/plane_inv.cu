@@ -10,11 +10,12 @@ __global__ void __launch_bounds__(PlaneCfg<T>::kMaxThreads, PlaneCfg<T>::kMinBlo
 plane_inv_kernel(const InvArgs<Tf, T> a) {
   constexpr int kBatch = PlaneCfg<T>::kBatch;
   const int s_ncomp = a.s_ncomp;
-  const T c0h = a.c0h, c0d = a.c0d;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Geo& g = a.g;
   const int z = blockIdx.x, c = blockIdx.y, lrhs = blockIdx.z, rhs = a.rhs0 + lrhs;
   if (a.st != nullptr && a.st[rhs].active == 0) return;
+  T c0h, c0d;
+  c0_weights<T>(a.c0, rve_of(rhs, a.rve_loads), a.c0h, a.c0d, c0h, c0d);
   const int n1 = g.n1, n2 = g.n2, h = g.h, P = g.P;
   cx<T>* pl = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* twh = pl + n2 * P + n2;   // rows: exp(-2 pi i t / h)

@@ -33,6 +33,43 @@ __device__ __forceinline__ int wave(int j, int n) {
   return k;
 }
 
+// Constants of green_from_w for the reference medium (lam0, mu0), or for c0[rve] when c0 is given:
+// c1 = 1 / (2 mu0), c2h = (lam0 + mu0) / (2 mu0 (lam0 + 2 mu0))
+template <typename T>
+__device__ __forceinline__ void green_consts(const double* c0, int rve, double lam0, double mu0, T& c1, T& c2h) {
+  if (c0 != nullptr) {
+    lam0 = c0[4 * rve];
+    mu0 = c0[4 * rve + 1];
+  }
+  c1 = (T)(1.0 / (2.0 * mu0));
+  c2h = (T)((lam0 + mu0) / (2.0 * mu0 * (lam0 + 2.0 * mu0)));
+}
+
+// The vector at which Gamma0_hat is evaluated for the half-spectrum frequency (kx, ky, n):
+//  green == 0: the discrete wave vector xi (Nyquist components 0);
+//  green == 1: the rotated finite-difference symbol q_j = sin(xi_j h/2) prod_{l != j} cos(xi_l h/2)
+//  from gtab = [sin | cos](pi j / N1), j <= N1/2, then [sin | cos](pi j / N2), [sin | cos](pi j / N3),
+//  j < N, by DFT index (cos exactly 0 at N/2).  Indices past N/2 flip sin and cos of an axis
+//  together, which flips q as a whole; Gamma0_hat is even, so the operator is unchanged.
+template <typename T>
+__device__ __forceinline__ void wave_vector(const Geo& g, int green, const double* gtab, int kx, int ky, int n,
+                                            T& x1, T& x2, T& x3) {
+  if (green == 0) {
+    x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
+    x2 = (T)(wave(ky, g.n2) * g.xs2);
+    x3 = (T)(wave(n, g.n3) * g.xs3);
+  } else {
+    const double* t2 = gtab + 2 * (g.h + 1);
+    const double* t3 = t2 + 2 * g.n2;
+    const double s1 = __ldg(gtab + kx), c1 = __ldg(gtab + g.h + 1 + kx);
+    const double s2 = __ldg(t2 + ky), c2 = __ldg(t2 + g.n2 + ky);
+    const double s3 = __ldg(t3 + n), c3 = __ldg(t3 + g.n3 + n);
+    x1 = (T)(s1 * c2 * c3);
+    x2 = (T)(c1 * s2 * c3);
+    x3 = (T)(c1 * c2 * s3);
+  }
+}
+
 // eta_hat = -Gamma0_hat(xi) : tau_hat in Kelvin components, given w = tau_hat xi.
 // Gamma0_hat : tau_hat = v (x) xi + xi (x) v with
 // v = w / (2 mu0 |xi|^2) - (lam0 + mu0) / (2 mu0 (lam0 + 2 mu0)) (xi . w) xi / |xi|^4,

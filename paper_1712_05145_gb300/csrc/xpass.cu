@@ -32,12 +32,15 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
 
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
+  const int rve = rve_of(rhs, a.rve_loads);
   if (a.mode != FWD_COPY && a.mode != FWD_C0) {
+    const T* mat = a.mat + (long long)rve * kRveTable;
     for (int i = tid; i < a.n_phase; i += nthr) {
-      tab[i] = a.mat[i * 4 + (c == 0 ? 0 : 1)];
-      tab[a.n_phase + i] = a.mat[i * 4 + (c == 0 ? 2 : 3)];
+      tab[i] = mat[i * 4 + (c == 0 ? 0 : 1)];
+      tab[a.n_phase + i] = mat[i * 4 + (c == 0 ? 2 : 3)];
     }
   }
+  const uint8_t* phase = a.phase + (long long)rve * g.M;
   __syncthreads();
 
   const long long cbase = (long long)(rhs * a.in_ncomp + c) * g.M;  // this component's field
@@ -55,7 +58,9 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
   const T beta = restart ? (T)0 : (T)sp->beta;
   const T ec = (a.E != nullptr && (a.mode == FWD_TAU || a.mode == FWD_STRESS)) ? (T)a.E[rhs * 6 + c] : (T)0;
   const T* w = (a.mode == FWD_TAU) ? tab : tab + a.n_phase;
-  const T wc = (a.mode == FWD_C0) ? (c == 0 ? a.c0h : a.c0d) : (T)1;
+  T ch, cd;
+  c0_weights<T>(a.c0, rve, a.c0h, a.c0d, ch, cd);
+  const T wc = (a.mode == FWD_C0) ? (c == 0 ? ch : cd) : (T)1;
 
 #pragma unroll 4
   for (int lr = warp; lr < rb; lr += nwarp) {
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
         if (a.mode == FWD_TAU || a.mode == FWD_STRESS) {
           Tf v0 = 0, v1 = 0;
           if (a.in != nullptr) ld2<Tf>(a.in + cbase + o, v0, v1);
-          const uchar2 ph = *reinterpret_cast<const uchar2*>(a.phase + o);
+          const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + o);
           val = mk<T>(w[ph.x] * ((T)v0 + ec), w[ph.y] * ((T)v1 + ec));
         } else if (a.mode == FWD_CG) {
           Tf r_0, r_1, p_0 = 0, p_1 = 0;
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
           if (!restart) ld2<Tf>(a.p + cbase + o, p_0, p_1);
           const T q0 = (T)r_0 + beta * (T)p_0, q1 = (T)r_1 + beta * (T)p_1;
           st2<Tf>(a.p + cbase + o, (Tf)q0, (Tf)q1);
-          const uchar2 ph = *reinterpret_cast<const uchar2*>(a.phase + o);
+          const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + o);
           const T c0 = tab[a.n_phase + ph.x], c1 = tab[a.n_phase + ph.y];
           acc += c0 * q0 * q0 + c1 * q1 * q1;
           val = mk<T>(c0 * q0, c1 * q1);
@@ -209,7 +214,9 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
   fft_pencils<T, +1, EPT>(pl, RowAddr{P}, h, rb, g.fd_rb, twh);
 
   T q0 = 0, q1 = 0;
-  const T cw = (c == 0) ? a.c0h : a.c0d;
+  T ch, cd;
+  c0_weights<T>(a.c0, rve_of(rhs, a.rve_loads), a.c0h, a.c0d, ch, cd);
+  const T cw = (c == 0) ? ch : cd;
   if (a.mode == INV_STORE) {
     const long long cbase = (long long)(rhs * a.out_ncomp + c) * g.M;
 #pragma unroll 4

@@ -67,8 +67,8 @@ __global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>
     cx<T>* part[kZcComps];
 #pragma unroll
     for (int r = 0; r < kZcComps; ++r) part[r] = cl.map_shared_rank(buf, r);
-    const T c1 = (T)(1.0 / (2.0 * a.mu0));
-    const T c2h = (T)((a.lam0 + a.mu0) / (2.0 * a.mu0 * (a.lam0 + 2.0 * a.mu0)));
+    T c1, c2h;
+    green_consts<T>(a.c0, rve_of(rhs, a.rve_loads), a.lam0, a.mu0, c1, c2h);
     const T scale = (T)a.scale;
     const long long nmain = (long long)g.n2 * g.h;
     const int share = (per + kZcComps - 1) / kZcComps;
@@ -80,10 +80,9 @@ __global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>
       int kx, ky;
       if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
       else { ky = (int)(f - nmain); kx = g.h; }
-      // discrete wave vector: Nyquist components taken as 0
-      const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
-      const T x2 = (T)(wave(ky, g.n2) * g.xs2);
-      const T x3 = (T)(wave(n, n3) * g.xs3);
+      // discrete wave vector (Nyquist components taken as 0), or the rotated difference symbol
+      T x1, x2, x3;
+      wave_vector<T>(g, a.green, a.gtab, kx, ky, n, x1, x2, x3);
       cx<T> k[6], tt[6], w1, w2, w3;
 #pragma unroll
       for (int i = 0; i < 6; ++i) k[i] = part[i][q];

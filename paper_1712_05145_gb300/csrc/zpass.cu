@@ -13,8 +13,8 @@ namespace hom {
 template <typename T>
 __global__ void __launch_bounds__(256) zgreen_kernel(const ZArgs<T> a, int nrhs) {
   const Geo& g = a.g;
-  const T c1 = (T)(1.0 / (2.0 * a.mu0));
-  const T c2h = (T)((a.lam0 + a.mu0) / (2.0 * a.mu0 * (a.lam0 + 2.0 * a.mu0)));
+  T c1, c2h;
+  green_consts<T>(nullptr, 0, a.lam0, a.mu0, c1, c2h);
   const T scale = (T)a.scale;
   const long long per = (long long)g.n3 * g.plane_c;   // frequencies of one component
   const long long nmain = (long long)g.n2 * g.h;
@@ -27,14 +27,14 @@ __global__ void __launch_bounds__(256) zgreen_kernel(const ZArgs<T> a, int nrhs)
        id += (long long)gridDim.x * blockDim.x) {
     const long long lrhs = id / per, q = id - lrhs * per;
     if (a.st != nullptr && a.st[a.rhs0 + lrhs].active == 0) continue;
+    if (a.c0 != nullptr) green_consts<T>(a.c0, rve_of(a.rhs0 + (int)lrhs, a.rve_loads), a.lam0, a.mu0, c1, c2h);
     const int n = (int)(q / g.plane_c);
     const long long f = q - (long long)n * g.plane_c;
     int kx, ky;
     if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
     else { ky = (int)(f - nmain); kx = g.h; }
-    const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
-    const T x2 = (T)(wave(ky, g.n2) * g.xs2);
-    const T x3 = (T)(wave(n, g.n3) * g.xs3);
+    T x1, x2, x3;
+    wave_vector<T>(g, a.green, a.gtab, kx, ky, n, x1, x2, x3);
     cx<T>* base = a.S + lrhs * 6 * per + q;
     cx<T> k[6], tt[6], w1, w2, w3;
 #pragma unroll
@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
   if (a.mode != Z_INV && a.mode != Z_GREEN) fft_pencils<T, -1, EPT>(buf, za, n3, a.ncomp_in * TC, a.fd_in, twz);
 
   if (a.mode == Z_GAMMA || a.mode == Z_GREEN || a.mode == Z_DISP || a.mode == Z_RHS) {
-    const T c1 = (T)(1.0 / (2.0 * a.mu0));
-    const T c2h = (T)((a.lam0 + a.mu0) / (2.0 * a.mu0 * (a.lam0 + 2.0 * a.mu0)));
+    T c1, c2h;
+    green_consts<T>(a.c0, rve_of(rhs, a.rve_loads), a.lam0, a.mu0, c1, c2h);
     const T scale = (T)a.scale;
     const long long nmain = (long long)g.n2 * g.h;
     for (int t = tid; t < n3 * TC; t += nthr) {
@@ -112,10 +112,9 @@ __global__ void __launch_bounds__(512) zpass_kernel(const ZArgs<T> a) {
       int kx, ky;
       if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
       else { ky = (int)(f - nmain); kx = g.h; }
-      // discrete wave vector: Nyquist components taken as 0
-      const T x1 = (T)((kx == g.h ? 0 : kx) * g.xs1);
-      const T x2 = (T)(wave(ky, g.n2) * g.xs2);
-      const T x3 = (T)(wave(n, n3) * g.xs3);
+      // discrete wave vector (Nyquist components taken as 0), or the rotated difference symbol
+      T x1, x2, x3;
+      wave_vector<T>(g, a.green, a.gtab, kx, ky, n, x1, x2, x3);
       const int e0 = n * TC + tc;
       cx<T> k[6], tt[6], w1, w2, w3;
 #pragma unroll

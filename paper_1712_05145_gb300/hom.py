@@ -34,6 +34,8 @@ HOM_POLARIZATION = 3
 HOM_FIELD_STRAIN = 0
 HOM_FIELD_DISPLACEMENT = 1
 HOM_FIELD_STRESS = 2
+HOM_GREEN_SPECTRAL = 0
+HOM_GREEN_ROTATED = 1
 
 HOM_KERNEL_PLANE_FWD = 0
 HOM_KERNEL_ZPASS = 1
@@ -45,8 +47,8 @@ KERNEL_NAMES = ["plane_fwd", "zpass", "plane_inv", "plane_fwd_f64", "zpass_f64",
 EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "hom_get_field",
             "hom_ls_apply", "hom_equilibrium_error", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
             "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
-            "hom_server_create", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
-            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_zpass_config", "hom_plane_config",
+            "hom_server_create", "hom_server_create_batched", "hom_server_counters", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
+            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_zpass_config", "hom_plane_config", "hom_set_rve",
             "hom_launch_count",
             "hom_last_error",
             "hom_status_string", "hom_destroy"]
@@ -58,7 +60,7 @@ class hom_options(ctypes.Structure):
                 ("spectrum_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("pass_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("polarization_variant", ctypes.c_int32), ("z_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("green_operator", ctypes.c_int32), ("n_rve", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -149,6 +151,10 @@ def load_library(path=None):
     lib.hom_estimate_bytes.restype = I64
     lib.hom_server_create.argtypes = [I64, I32, ctypes.POINTER(V)]
     lib.hom_server_create.restype = I32
+    lib.hom_server_create_batched.argtypes = [I64, I32, I32, ctypes.POINTER(V)]
+    lib.hom_server_create_batched.restype = I32
+    lib.hom_server_counters.argtypes = [V, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.hom_server_counters.restype = I32
     lib.hom_server_submit.argtypes = [V, ctypes.POINTER(hom_request), ctypes.POINTER(I64)]
     lib.hom_server_submit.restype = I32
     lib.hom_server_poll.argtypes = [V, I64, ctypes.POINTER(hom_result)]
@@ -163,6 +169,8 @@ def load_library(path=None):
     lib.hom_device_bytes.restype = I64
     lib.hom_launch_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.hom_launch_config.restype = ctypes.c_int
+    lib.hom_set_rve.argtypes = [V, I32, V, I32, V, ctypes.c_double, ctypes.c_double]
+    lib.hom_set_rve.restype = I32
     lib.hom_plane_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32)]
     lib.hom_plane_config.restype = ctypes.c_int
     lib.hom_zpass_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
@@ -229,11 +237,14 @@ def loads_of_order(order):
     return 6 if order == 0 else 6 * (order + 1) * (order + 2) // 2
 
 
-def hom_solve(h, order, tol, loads=None):
+def hom_solve(h, order, tol, loads=None, n_loads=None):
     """Returns a list of per-load info dicts; raises HomError on any failure except
-    non-convergence, which is reported through each load's status."""
+    non-convergence, which is reported through each load's status.  n_loads (with loads None)
+    is the load count of a handle with several RVE slots: 6 x the slots to solve."""
     lib = load_library()
     nl = loads_of_order(order) if loads is None else int(np.asarray(loads).shape[0])
+    if loads is None and n_loads is not None:
+        nl = int(n_loads)
     arr = None
     if loads is not None:
         arr = np.ascontiguousarray(loads, dtype=np.float64).reshape(nl, 6 if order == 0 else 18)
@@ -319,9 +330,11 @@ def hom_estimate_bytes(grid, order, precision=HOM_FP32_REFINE):
     return int(load_library().hom_estimate_bytes(g, int(order), int(precision)))
 
 
-def hom_server_create(budget_bytes=0, max_active=4):
+def hom_server_create(budget_bytes=0, max_active=4, max_batch=8):
+    """A request server; max_batch order-0 requests of one grid share a handle and its launches."""
     s = ctypes.c_void_p()
-    st = load_library().hom_server_create(int(budget_bytes), int(max_active), ctypes.byref(s))
+    st = load_library().hom_server_create_batched(int(budget_bytes), int(max_active), int(max_batch),
+                                                  ctypes.byref(s))
     if st != HOM_OK:
         raise HomError(st, "hom_server_create")
     return s
@@ -364,6 +377,13 @@ def hom_server_stats(s):
     return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
 
 
+def hom_server_counters(s):
+    """Batches run, requests run in them and handles created by a server so far."""
+    b, r, h = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(None, load_library().hom_server_counters(s, ctypes.byref(b), ctypes.byref(r), ctypes.byref(h)))
+    return {"batches": b.value, "requests": r.value, "handles_created": h.value}
+
+
 def hom_server_destroy(s):
     if s:
         load_library().hom_server_destroy(s)
@@ -378,6 +398,15 @@ def hom_launch_config(h):
     a, b = ctypes.c_int32(), ctypes.c_int32()
     _check(h, load_library().hom_launch_config(h, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def hom_set_rve(h, slot, phase, lame, lambda0, mu0):
+    """Replaces RVE slot `slot` of a handle (phase uint8 [N3][N2][N1] numpy or torch, lame [n][2])."""
+    lame = np.ascontiguousarray(lame, dtype=np.float64)
+    if isinstance(phase, np.ndarray):
+        phase = np.ascontiguousarray(phase, dtype=np.uint8)
+    _check(h, load_library().hom_set_rve(h, int(slot), _ptr(phase), int(lame.shape[0]), _ptr(lame),
+                                         float(lambda0), float(mu0)))
 
 
 def hom_plane_config(h):
@@ -416,7 +445,7 @@ class Homogenization:
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
                  max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,
-                 pass_mode=0, autotune=0, polarization_variant=0, z_mode=0):
+                 pass_mode=0, autotune=0, polarization_variant=0, z_mode=0, green_operator=0, n_rve=1):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
         self.M = n1 * n2 * n3
@@ -433,6 +462,8 @@ class Homogenization:
         opt.autotune = autotune
         opt.polarization_variant = polarization_variant
         opt.z_mode = z_mode
+        opt.green_operator = green_operator
+        opt.n_rve = n_rve
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
                             ms.mu0 if mu0 is None else mu0, opt)
         self.nloads = {}
@@ -448,8 +479,8 @@ class Homogenization:
         except Exception:
             pass
 
-    def solve(self, order, tol, loads=None):
-        info = hom_solve(self.h, order, tol, loads)
+    def solve(self, order, tol, loads=None, n_loads=None):
+        info = hom_solve(self.h, order, tol, loads, n_loads)
         self.nloads[order] = len(info)
         return info
 

@@ -55,6 +55,27 @@ def test_mixed_requests_match_solo_solves():
             np.testing.assert_allclose(r["d1"], d, rtol=0, atol=1e-12 * max(np.abs(d).max(), 1e-30))
 
 
+def test_same_grid_requests_share_launches_and_handles():
+    """Order-0 requests of one grid queued together run as one batch (one handle, every launch
+    carrying all their loads); a later wave reuses the resident handle; results are the solo ones."""
+    from paper_1712_05145_gb300 import hom
+    tol = 1e-7
+    reqs = [synthetic.random_spheres((16, 16, 16), seed=50 + k, inclusion_e=3.0 * 10 ** (k % 3)) for k in range(6)]
+    ref = [solo(ms, 0, tol)[0] for ms in reqs]
+    s = hom.hom_server_create(0, 1, 8)
+    for wave in range(2):
+        ids = [hom.hom_server_submit(s, ms, 0, tol) for ms in reqs]
+        res = [hom.hom_server_wait(s, i) for i in ids]
+        for c, r in zip(ref, res):
+            assert r["status"] == 0, r["message"]
+            np.testing.assert_allclose(r["c_eff"], c, rtol=0, atol=1e-12 * np.abs(c).max())
+    cnt = hom.hom_server_counters(s)
+    hom.hom_server_destroy(s)
+    assert cnt["requests"] == 12
+    assert cnt["batches"] < cnt["requests"]          # some requests shared a batch
+    assert cnt["handles_created"] <= 2               # the second wave ran on resident handles
+
+
 def test_admission_respects_the_memory_budget():
     from paper_1712_05145_gb300 import hom
     ms = synthetic.random_spheres((32, 32, 32), seed=4)
