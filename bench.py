@@ -321,6 +321,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the 128^3 configuration and the oracle checks")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--serving-baseline", type=int, default=30)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -406,6 +409,15 @@ def main():
             "launch_shape": {"loads_per_launch": hom.hom_launch_config(H2.h)[0],
                              "zpass_cluster_tile_log2": hom.hom_zpass_config(H2.h)}}
         H2.close()
+
+    if not args.no_extras and not args.no_serving:
+        # the serving configuration, bounded: a Poisson stream of mixed grids and orders
+        from paper_1712_05145_gb300 import serving
+        extras["serving"] = serving.serve_benchmark(args.serving_requests, capacity_requests=args.serving_requests // 2,
+                                                    baseline_requests=args.serving_baseline)
+        extras["serving"]["note"] = ("grids {32,48,64,96,128}^3 and 32x64x128, orders 0/1, contrast log-uniform "
+                                     "[2,1000], Poisson arrivals at 0.8 x measured capacity; fp64_sequential is the "
+                                     "plain FP64 one-solve-per-handle form on the first requests of the same stream")
 
     # end to end through the C ABI with host buffers: create from host arrays, solve, read C_eff
     e2e = None

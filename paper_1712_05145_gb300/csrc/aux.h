@@ -12,6 +12,9 @@ cudaError_t launch_kelvin_to_mandel(const Tf* in, double* out, long long M, int 
 cudaError_t launch_mandel_to_kelvin_inplace(double* f, long long M, int nf, cudaStream_t s);
 // Kelvin -> Mandel of FP64 fields [nf][6][M] in place
 cudaError_t launch_kelvin_to_mandel_inplace(double* f, long long M, int nf, cudaStream_t s);
+// x += alpha p per load where the load's CG state has an update pending (RhsState::xpend)
+template <typename Tf>
+cudaError_t launch_cg_flush(Tf* x, const Tf* p, const RhsState* st, long long per, int n, cudaStream_t s);
 // x[i] += d[i] for i < n
 cudaError_t launch_add_correction(const float* d, double* x, long long n, cudaStream_t s);
 // x += a - b

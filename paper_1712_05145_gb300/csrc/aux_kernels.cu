@@ -77,6 +77,20 @@ __global__ void mandel_to_kelvin_inplace_kernel(double* f, long long M, int nf) 
   }
 }
 
+// x += alpha p for each load whose CG state has an update of x pending (the update the next
+// forward pass would otherwise apply), fields [n][per]
+template <typename Tf>
+__global__ void cg_flush_kernel(Tf* __restrict__ x, const Tf* __restrict__ p, const RhsState* __restrict__ st,
+                                long long per) {
+  const int l = blockIdx.y;
+  if (st[l].xpend == 0) return;
+  const Tf alpha = (Tf)st[l].alpha;
+  Tf* xl = x + (long long)l * per;
+  const Tf* pl = p + (long long)l * per;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per; i += (long long)gridDim.x * blockDim.x)
+    xl[i] = xl[i] + alpha * pl[i];
+}
+
 template <typename Ti, typename To>
 __global__ void convert_kernel(const Ti* __restrict__ in, To* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -113,6 +127,17 @@ cudaError_t launch_mandel_to_kelvin_inplace(double* f, long long M, int nf, cuda
   mandel_to_kelvin_inplace_kernel<<<grid_for(M * nf, 256), 256, 0, s>>>(f, M, nf);
   return cudaGetLastError();
 }
+template <typename Tf>
+cudaError_t launch_cg_flush(Tf* x, const Tf* p, const RhsState* st, long long per, int n, cudaStream_t s) {
+  long long b = (per + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  count_launch();
+  cg_flush_kernel<Tf><<<dim3((unsigned)b, (unsigned)n), 256, 0, s>>>(x, p, st, per);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_flush<float>(float*, const float*, const RhsState*, long long, int, cudaStream_t);
+template cudaError_t launch_cg_flush<double>(double*, const double*, const RhsState*, long long, int, cudaStream_t);
+
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long long n, cudaStream_t s) {
   count_launch();

@@ -589,9 +589,11 @@ hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<i
 
 // Autotuner (hom_options.autotune): times one operator application per candidate launch shape
 // on this handle's grid and keeps the fastest per load.  The candidates are the loads per launch
-// (1, 2, 3, 4, 6, 8, 12, ... up to the spectrum scratch's capacity, at most 12) and the z stages
-// that fit: the single-CTA z pass with tiles of 2^0 .. 2^4 columns and the cluster z pass with
-// tiles of at least 32 bytes per z-plane.  It tunes the passes of the iteration precision T.
+// (1, 2, 3, 4, 6, 8, 12, ... up to the spectrum scratch's capacity, at most 12), the z stages
+// that fit (the single-CTA z pass with tiles of 2^0 .. 2^4 columns, the cluster z pass with tiles
+// of at least 32 bytes per z-plane) and, on planes above one CTA, the cluster plane passes against
+// the split x and y passes; then the split y pass's tile width.  It tunes the passes of the
+// iteration precision T.
 template <typename T>
 hom_status autotune(hom_ctx* c) {
   const int nt = std::min(c->chunk, 12);
@@ -658,8 +660,6 @@ hom_status autotune(hom_ctx* c) {
     }
   }
   c->pc_off = best_pc_off;
-  c->ev_pool.push_back(e0);
-  c->ev_pool.push_back(e1);
   c->chunk = best_chunk;
   c->zc_off[idx] = (best_kind == 0);
   if (best_kind == 0) {
@@ -669,6 +669,30 @@ hom_status autotune(hom_ctx* c) {
     c->zc_lg[idx] = best_lg;
     c->ztile_lg[idx] = -1;
   }
+  // then, where the split y pass runs, its tile width (2^2 .. 2^4 columns) with the rest fixed
+  if (c->g.split && (c->g.pc_Q == 0 || c->pc_off || !std::is_same<T, float>::value)) {
+    const int lg0 = c->g.ty_log2;
+    int best_y = lg0;
+    for (int lg = 2; lg <= 4; ++lg) {
+      if (lg == lg0 || !ytile_fits(c->g, lg)) continue;
+      set_ytile(c->g, lg);
+      CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));
+      CK(cudaEventRecord(e0, c->stream));
+      for (int rep = 0; rep < 2; ++rep)
+        CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_y = lg;
+      }
+    }
+    set_ytile(c->g, best_y);
+  }
+  c->ev_pool.push_back(e0);
+  c->ev_pool.push_back(e1);
   c->tuned = true;
   return HOM_OK;
 }
@@ -1010,21 +1034,28 @@ hom_status solve_system(hom_ctx* c, int n, const double* dE, const double* b64, 
           auto fa = fwd_args<Tf, Tf>(c, FWD_CG, 6, 6);
           fa.r = r;
           fa.p = p;
+          fa.x = d;
           fa.st = c->d_st;
           auto za = z_args<Tf>(c, Z_GAMMA, 6, 6);
           za.st = c->d_st;
           auto ia = inv_args<Tf, Tf>(c, INV_CG, FIN_CG, 6, 6, 6);
-          ia.p = p;
-          ia.x = d;
           ia.r = r;
           ia.st = c->d_st;
           CKS((ls_pass<Tf, Tf, Tf>(c, n, fa, za, ia, &act)));
         }
         CKS(read_states(c, n, st));
         any = false;
+        bool pend = false;
         for (int i = 0; i < n; ++i) {
           act[i] = st[i].active;
           any = any || act[i];
+          pend = pend || (!act[i] && st[i].xpend);
+        }
+        if (!any && pend) {
+          // the last iteration's x += alpha p, which a following forward pass would have applied
+          CK(launch_cg_flush<Tf>(d, p, c->d_st, 6 * c->g.M, n, c->stream));
+          for (int i = 0; i < n; ++i) st[i].xpend = 0;
+          CKS(write_states(c, st));
         }
       }
       if (mixed) {  // x += d, d = 0

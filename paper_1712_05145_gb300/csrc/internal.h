@@ -54,11 +54,14 @@ struct RhsState {
   double rr;
   int sconv;         // 1: the half step s already met the tolerance (omega = 0, x += alpha p)
   int stall;         // 1: end the sweep when the residual stalls (FP32 sweeps of the refinement)
+  int xpend;         // CG: x += alpha p of the last iteration is still to be applied (the next
+                     // forward pass applies it while it reads p; after a sweep, cg_flush does)
 };
 
 // FWD_TAU: tau = (C - C0) : (in + E)     (polarization, Eq. auxiliary_problem)
 // FWD_STRESS: tau = C : (in + E)         (stress; -Gamma0 * sigma is the equilibrium residual)
-// FWD_CG: p = r + beta p, tau = C : p    (CG direction; A p = Gamma0 * (C : p) on compatible p)
+// FWD_CG: x += alpha p, p = r + beta p, tau = C : p   (CG: the previous iteration's update of x and
+//         the new direction; A p = Gamma0 * (C : p) on compatible p)
 // FWD_COPY: tau = in                     (plain transform)
 // FWD_C0: tau = C0 : in                  (-Gamma0 * (C0 : in) is minus the compatible part of in)
 enum FwdMode { FWD_TAU = 0, FWD_CG = 1, FWD_COPY = 2, FWD_STRESS = 3, FWD_C0 = 4 };
@@ -85,6 +88,7 @@ struct FwdArgs {
   const double* E;             // FWD_TAU: [rhs][6] Kelvin macroscopic strain (nullable)
   const Tf* r;                 // FWD_CG
   Tf* p;                       // FWD_CG (read old p, write new p)
+  Tf* x;                       // FWD_CG (x += alpha p with the old p, except at a restart)
   cx<T>* S;                    // chunk spectrum
   int rhs0;                    // global rhs index of the chunk's first rhs
   RhsState* st;                // nullable
@@ -134,9 +138,7 @@ struct InvArgs {
   const double* b;       // INV_STORE: added right-hand-side field, FP64 (nullable)
   const double* xsub;    // INV_STORE: subtracted field, FP64 (nullable): out = scale*eta + b - xsub
   const Tf* prev;        // INV_STORE: previous iterate for the Cauchy difference (nullable)
-  const Tf* p;           // INV_CG
-  Tf* x;                 // INV_CG
-  Tf* r;                 // INV_CG
+  Tf* r;                 // INV_CG: r += alpha eta (= r - alpha A p)
   RhsState* st;
   double* part;
   unsigned* cnt;
@@ -179,6 +181,9 @@ size_t plane_smem_bytes(const Geo& g, size_t elem);
 size_t zpass_smem_bytes(const Geo& g, size_t elem, int ncomp, int tc_log2);
 // fills fd_h, fd_n2 and the split-pass tiling of a geometry whose n1, n2, n3 are set
 void geo_finish(Geo& g);
+// y pass tiles of 2^lg columns (ty_log2, thr_y, fd_ty); whether such tiles fit the y pass
+void set_ytile(Geo& g, int lg);
+bool ytile_fits(const Geo& g, int lg);
 // resident CTAs per SM of the z pass for a launch shape (occupancy query, cached)
 template <typename T>
 int zpass_ctas_per_sm(int threads, size_t smem);

@@ -148,6 +148,7 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
     case FIN_ENERGY: {
       const double pAp = v[0] * invM;
       s.pAp = pAp;
+      s.xpend = 0;   // this forward pass applied the previous iteration's update of x
       s.alpha = (pAp != 0.0) ? s.rho / pAp : 0.0;
       if (!isfinite(s.alpha)) { s.status = 2; s.active = 0; }
       break;
@@ -159,6 +160,7 @@ __device__ __forceinline__ void finalize_state(int kind, RhsState& s, const doub
       s.res = (s.b2 > 0.0) ? sqrt(rr / s.b2) : 0.0;
       s.iter += 1;
       s.restart = 0;
+      s.xpend = 1;
       if (!isfinite(s.res) || !isfinite(s.beta)) { s.status = 2; s.active = 0; }
       else if (s.res < s.tol) s.active = 0;
       else if (s.iter >= s.max_iter) { s.active = 0; s.status = 1; }

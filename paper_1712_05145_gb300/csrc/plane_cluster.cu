@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
   const long long foff = ((long long)(rhs * a.in_ncomp + c) * g.n3 + z) * plane_sz + (long long)y0 * n1;
   const long long blk_sz = (long long)R * n1;             // voxels of this CTA's rows
   if (a.prof != nullptr && tid == 0) {
-    long long fields = (a.mode == FWD_CG) ? 3 : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
+    long long fields = (a.mode == FWD_CG) ? (a.st[rhs].restart ? 2 : 5)
+                                          : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
     long long b = fields * blk_sz * (long long)sizeof(Tf) + (long long)n2 * Cb * (long long)sizeof(cx<T>);
     if (q == 0) b += (long long)n2 * (long long)sizeof(cx<T>);
     if (a.mode != FWD_COPY && a.mode != FWD_C0) b += blk_sz;
@@ -108,10 +109,12 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
     const RhsState& s = a.st[rhs];
     const bool restart = (s.restart != 0);
     const T beta = restart ? (T)0 : (T)s.beta;
+    const T alpha = restart ? (T)0 : (T)s.alpha;
     const Tf* rp = a.r + foff;
     Tf* pp = a.p + foff;
+    Tf* xp = a.x + foff;
     for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
-      Tf r0[kBatch], r1[kBatch], p0[kBatch], p1[kBatch];
+      Tf r0[kBatch], r1[kBatch], p0[kBatch], p1[kBatch], x0[kBatch], x1[kBatch];
       uchar2 ph[kBatch];
       int rw[kBatch];
 #pragma unroll
@@ -123,7 +126,10 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
         if (e < total) {
           const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
           ld2<Tf>(rp + o, r0[j], r1[j]);
-          if (!restart) ld2<Tf>(pp + o, p0[j], p1[j]);
+          if (!restart) {   // a restart neither reads the old p nor has an update of x pending
+            ld2<Tf>(pp + o, p0[j], p1[j]);
+            ld2<Tf>(xp + o, x0[j], x1[j]);
+          }
           ph[j] = *reinterpret_cast<const uchar2*>(php + o);
         }
       }
@@ -132,6 +138,7 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_fwd_cluster_kernel(con
         const int e = e0 + j * nthr;
         if (e < total) {
           const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
+          if (!restart) st2<Tf>(xp + o, (Tf)((T)x0[j] + alpha * (T)p0[j]), (Tf)((T)x1[j] + alpha * (T)p1[j]));
           const T q0 = (T)r0[j] + beta * (T)p0[j];
           const T q1 = (T)r1[j] + beta * (T)p1[j];
           st2<Tf>(pp + o, (Tf)q0, (Tf)q1);
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_inv_cluster_kernel(con
   const long long plane_sz = (long long)n2 * n1;
   const long long blk_sz = (long long)R * n1;
   if (a.prof != nullptr && tid == 0) {
-    long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
+    long long fields = (a.mode == INV_CG) ? 2 : 1 + (a.fin == FIN_BASIC);
     long long b = fields * blk_sz * (long long)sizeof(Tf) + (long long)n2 * Cb * (long long)sizeof(cx<T>);
     if (q == 0) b += (long long)n2 * (long long)sizeof(cx<T>);
     if (a.b != nullptr) b += blk_sz * (long long)sizeof(double);
@@ -379,15 +386,13 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_inv_cluster_kernel(con
       q1 += v0 * v0 + v1 * v1;
       st2<Tf>(a.out + o, (Tf)v0, (Tf)v1);
     }
-  } else {  // INV_CG: q = A p = Gamma0 * (C : p) = -eta, x += alpha p, r -= alpha q
+  } else {  // INV_CG: q = A p = Gamma0 * (C : p) = -eta, r -= alpha q (x += alpha p: next forward pass)
     const long long foff = ((long long)(rhs * 6 + c) * g.n3 + z) * plane_sz + (long long)y0 * n1;
     const T alpha = (T)a.st[rhs].alpha;
     const T cw = (c == 0) ? c0h : c0d;
-    const Tf* pp = a.p + foff;
-    Tf* xp = a.x + foff;
     Tf* rp = a.r + foff;
     for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
-      Tf p0[kBatch], p1[kBatch], x0[kBatch], x1[kBatch], r0[kBatch], r1[kBatch];
+      Tf r0[kBatch], r1[kBatch];
       int rw[kBatch];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
@@ -395,8 +400,6 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_inv_cluster_kernel(con
         rw[j] = (int)g.fd_h.div((unsigned)e);
         if (e < total) {
           const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
-          ld2<Tf>(pp + o, p0[j], p1[j]);
-          ld2<Tf>(xp + o, x0[j], x1[j]);
           ld2<Tf>(rp + o, r0[j], r1[j]);
         }
       }
@@ -406,9 +409,7 @@ __global__ void __launch_bounds__(kPcMaxThreads, 1) plane_inv_cluster_kernel(con
         if (e < total) {
           const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
           const cx<T> v = buf[rw[j] * P + col];
-          const T xa = (T)x0[j] + alpha * (T)p0[j], xb = (T)x1[j] + alpha * (T)p1[j];
           const T ra = (T)r0[j] + alpha * v.re, rb = (T)r1[j] + alpha * v.im;
-          st2<Tf>(xp + o, (Tf)xa, (Tf)xb);
           st2<Tf>(rp + o, (Tf)ra, (Tf)rb);
           q0 += cw * (ra * ra + rb * rb);
           q1 += ra * ra + rb * rb;

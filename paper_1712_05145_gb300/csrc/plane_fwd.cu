@@ -36,7 +36,10 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
     if (tid == 0 && (pb & 15u) == 0) {
       if (a.mode == FWD_CG) {
         prefetch_l2(a.r + fo, pb);
-        if (a.st[rhs].restart == 0) prefetch_l2(a.p + fo, pb);
+        if (a.st[rhs].restart == 0) {
+          prefetch_l2(a.p + fo, pb);
+          prefetch_l2(a.x + fo, pb);
+        }
       } else if (a.in != nullptr) {
         prefetch_l2(a.in + fo, pb);
       }
@@ -59,7 +62,8 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
   const long long foff = ((long long)(rhs * a.in_ncomp + c) * g.n3 + z) * plane_sz;
   if (a.prof != nullptr && tid == 0) {
     // algorithmic bytes: field planes read/written once, phase bytes, spectrum plane written
-    long long fields = (a.mode == FWD_CG) ? 3 : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
+    long long fields = (a.mode == FWD_CG) ? (a.st[rhs].restart ? 2 : 5)
+                                          : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
     long long b = fields * plane_sz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>);
     if (a.mode != FWD_COPY && a.mode != FWD_C0) b += plane_sz;
     atomicAdd(a.prof, (unsigned long long)b);
@@ -87,11 +91,13 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
     const RhsState& s = a.st[rhs];
     const bool restart = (s.restart != 0);
     const T beta = restart ? (T)0 : (T)s.beta;
+    const T alpha = restart ? (T)0 : (T)s.alpha;
     const Tf* rp = a.r + foff;
     Tf* pp = a.p + foff;
+    Tf* xp = a.x + foff;
     const int total = n2 * h;
     for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
-      Tf r0[kBatch], r1[kBatch], p0[kBatch], p1[kBatch];
+      Tf r0[kBatch], r1[kBatch], p0[kBatch], p1[kBatch], x0[kBatch], x1[kBatch];
       uchar2 ph[kBatch];
       int rw[kBatch];
       #pragma unroll
@@ -103,7 +109,10 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
         if (e < total) {
           const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
           ld2<Tf>(rp + o, r0[j], r1[j]);
-          if (!restart) ld2<Tf>(pp + o, p0[j], p1[j]);   // a restart never reads the old p
+          if (!restart) {   // a restart neither reads the old p nor has an update of x pending
+            ld2<Tf>(pp + o, p0[j], p1[j]);
+            ld2<Tf>(xp + o, x0[j], x1[j]);
+          }
           ph[j] = *reinterpret_cast<const uchar2*>(php + o);
         }
       }
@@ -112,6 +121,7 @@ plane_fwd_kernel(const FwdArgs<Tf, T> a) {
         const int e = e0 + j * nthr;
         if (e < total) {
           const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
+          if (!restart) st2<Tf>(xp + o, (Tf)((T)x0[j] + alpha * (T)p0[j]), (Tf)((T)x1[j] + alpha * (T)p1[j]));
           const T q0 = (T)r0[j] + beta * (T)p0[j];
           const T q1 = (T)r1[j] + beta * (T)p1[j];
           st2<Tf>(pp + o, (Tf)q0, (Tf)q1);
@@ -227,6 +237,14 @@ void geo_finish(Geo& g) {
   g.fd_rb = make_fastdiv((unsigned)g.rb);
   int lg = 0;
   while (lg < 4 && (g.h % (2 << lg)) == 0 && (long long)g.n2 * (2 << lg) <= (long long)kEPT * 512) ++lg;
+  set_ytile(g, lg);
+}
+
+bool ytile_fits(const Geo& g, int lg) {
+  return lg >= 0 && lg <= 4 && (g.h % (1 << lg)) == 0 && (long long)g.n2 * (1 << lg) <= (long long)kEPT * 512;
+}
+
+void set_ytile(Geo& g, int lg) {
   g.ty_log2 = lg;
   int ty = (int)(((long long)g.n2 * (1 << lg) + kEPT - 1) / kEPT);
   ty = ((ty + 31) / 32) * 32;

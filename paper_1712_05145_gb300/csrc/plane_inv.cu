@@ -33,8 +33,6 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
     if (tid == 0 && (pb & 15u) == 0) {
       if (a.mode == INV_CG) {
         const long long fo = ((long long)(rhs * 6 + c) * g.n3 + z) * psz;
-        prefetch_l2(a.p + fo, pb);
-        prefetch_l2(a.x + fo, pb);
         prefetch_l2(a.r + fo, pb);
       } else {
         const long long fo = ((long long)(rhs * a.out_ncomp + c) * g.n3 + z) * psz;
@@ -61,7 +59,7 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
 
   if (a.prof != nullptr && tid == 0) {
     const long long psz = (long long)n2 * n1;
-    long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
+    long long fields = (a.mode == INV_CG) ? 2 : 1 + (a.fin == FIN_BASIC);
     long long b = fields * psz * (long long)sizeof(Tf) + g.plane_c * (long long)sizeof(cx<T>);
     if (a.b != nullptr) b += psz * (long long)sizeof(double);
     if (a.xsub != nullptr) b += psz * (long long)sizeof(double);
@@ -130,19 +128,17 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
         st2<Tf>(a.out + o, (Tf)v0, (Tf)v1);
       }
     }
-  } else {  // INV_CG: q = A p = Gamma0 * (C : p) = -eta, x += alpha p, r -= alpha q
+  } else {  // INV_CG: q = A p = Gamma0 * (C : p) = -eta, r -= alpha q (x += alpha p: next forward pass)
     // Flat element index e = row * h + col; each thread issues the loads of kBatch elements
-    // before the first store, so that they are in flight together (the stores to x and r
-    // may alias p for the compiler, which would otherwise serialise load -> store chains).
+    // before the first store, so that they are in flight together (a store to r may alias the
+    // next load for the compiler, which would otherwise serialise load -> store chains).
     const long long foff = ((long long)(rhs * 6 + c) * g.n3 + z) * plane_sz;
     const T alpha = (T)a.st[rhs].alpha;
     const T cw = (c == 0) ? c0h : c0d;
-    const Tf* pp = a.p + foff;
-    Tf* xp = a.x + foff;
     Tf* rp = a.r + foff;
     const int total = n2 * h;
     for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
-      Tf p0[kBatch], p1[kBatch], x0[kBatch], x1[kBatch], r0[kBatch], r1[kBatch];
+      Tf r0[kBatch], r1[kBatch];
       int rw[kBatch];
       #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
@@ -150,8 +146,6 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
         rw[j] = (int)g.fd_h.div((unsigned)e);
         if (e < total) {
           const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
-          ld2<Tf>(pp + o, p0[j], p1[j]);
-          ld2<Tf>(xp + o, x0[j], x1[j]);
           ld2<Tf>(rp + o, r0[j], r1[j]);
         }
       }
@@ -161,9 +155,7 @@ plane_inv_kernel(const InvArgs<Tf, T> a) {
         if (e < total) {
           const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
           const cx<T> v = pl[rw[j] * P + col];
-          const T xa = (T)x0[j] + alpha * (T)p0[j], xb = (T)x1[j] + alpha * (T)p1[j];
           const T ra = (T)r0[j] + alpha * v.re, rb = (T)r1[j] + alpha * v.im;
-          st2<Tf>(xp + o, (Tf)xa, (Tf)xb);
           st2<Tf>(rp + o, (Tf)ra, (Tf)rb);
           q0 += cw * (ra * ra + rb * rb);
           q1 += ra * ra + rb * rb;

@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
   const long long cbase = (long long)(rhs * a.in_ncomp + c) * g.M;  // this component's field
   if (a.prof != nullptr && tid == 0) {
     const long long vox = (long long)nr * n1;
-    long long fields = (a.mode == FWD_CG) ? 3 : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
+    long long fields = (a.mode == FWD_CG) ? (a.st[rhs].restart ? 2 : 5)
+                                          : ((a.mode == FWD_COPY || a.mode == FWD_C0 || a.in != nullptr) ? 1 : 0);
     long long b = fields * vox * (long long)sizeof(Tf) + (long long)nr * h * (long long)sizeof(cx<T>);
     if (a.mode != FWD_COPY && a.mode != FWD_C0) b += vox;
     atomicAdd(a.prof, (unsigned long long)b);
@@ -56,40 +57,81 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
   const RhsState* sp = (a.mode == FWD_CG) ? a.st + rhs : nullptr;
   const bool restart = sp ? (sp->restart != 0) : true;
   const T beta = restart ? (T)0 : (T)sp->beta;
+  const T alpha = restart ? (T)0 : (T)sp->alpha;
   const T ec = (a.E != nullptr && (a.mode == FWD_TAU || a.mode == FWD_STRESS)) ? (T)a.E[rhs * 6 + c] : (T)0;
   const T* w = (a.mode == FWD_TAU) ? tab : tab + a.n_phase;
   T ch, cd;
   c0_weights<T>(a.c0, rve, a.c0h, a.c0d, ch, cd);
   const T wc = (a.mode == FWD_C0) ? (c == 0 ? ch : cd) : (T)1;
 
-#pragma unroll 4
-  for (int lr = warp; lr < rb; lr += nwarp) {
-    for (int c2 = lane; c2 < h; c2 += 32) {
-      cx<T> val = mk<T>(0, 0);
-      if (lr < nr) {
-        const long long o = (r0 + lr) * n1 + 2 * c2;
-        if (a.mode == FWD_TAU || a.mode == FWD_STRESS) {
-          Tf v0 = 0, v1 = 0;
-          if (a.in != nullptr) ld2<Tf>(a.in + cbase + o, v0, v1);
-          const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + o);
-          val = mk<T>(w[ph.x] * ((T)v0 + ec), w[ph.y] * ((T)v1 + ec));
-        } else if (a.mode == FWD_CG) {
-          Tf r_0, r_1, p_0 = 0, p_1 = 0;
-          ld2<Tf>(a.r + cbase + o, r_0, r_1);
-          if (!restart) ld2<Tf>(a.p + cbase + o, p_0, p_1);
-          const T q0 = (T)r_0 + beta * (T)p_0, q1 = (T)r_1 + beta * (T)p_1;
-          st2<Tf>(a.p + cbase + o, (Tf)q0, (Tf)q1);
-          const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + o);
-          const T c0 = tab[a.n_phase + ph.x], c1 = tab[a.n_phase + ph.y];
-          acc += c0 * q0 * q0 + c1 * q1 * q1;
-          val = mk<T>(c0 * q0, c1 * q1);
-        } else {
-          Tf v0, v1;
-          ld2<Tf>(a.in + cbase + o, v0, v1);
-          val = mk<T>(wc * (T)v0, wc * (T)v1);
+  if (a.mode == FWD_CG) {
+    // Flat index e = row * h + col over this block's rows (contiguous in the field); the loads of
+    // kBatch elements per thread are issued before the first store of p, which the compiler must
+    // assume may alias r, so that they are in flight together.
+    constexpr int kBatch = PlaneCfg<T>::kBatch;
+    const Tf* rp = a.r + cbase + r0 * n1;
+    Tf* pp = a.p + cbase + r0 * n1;
+    Tf* xp = a.x + cbase + r0 * n1;
+    const uint8_t* php = phase + r0 * n1;
+    const int total = nr * h;
+    for (int e0 = tid; e0 < rb * h; e0 += kBatch * nthr) {
+      Tf q0r[kBatch], q1r[kBatch], p0[kBatch], p1[kBatch], x0[kBatch], x1[kBatch];
+      uchar2 ph[kBatch];
+      int rw[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        rw[j] = (int)g.fd_h.div((unsigned)e);
+        p0[j] = 0;
+        p1[j] = 0;
+        if (e < total) {
+          const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
+          ld2<Tf>(rp + o, q0r[j], q1r[j]);
+          if (!restart) {   // a restart neither reads the old p nor has an update of x pending
+            ld2<Tf>(pp + o, p0[j], p1[j]);
+            ld2<Tf>(xp + o, x0[j], x1[j]);
+          }
+          ph[j] = *reinterpret_cast<const uchar2*>(php + o);
         }
       }
-      pl[lr * P + c2] = val;
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        if (e >= rb * h) continue;
+        const int col = e - rw[j] * h;
+        cx<T> val = mk<T>(0, 0);
+        if (e < total) {
+          const int o = rw[j] * n1 + 2 * col;
+          if (!restart) st2<Tf>(xp + o, (Tf)((T)x0[j] + alpha * (T)p0[j]), (Tf)((T)x1[j] + alpha * (T)p1[j]));
+          const T q0 = (T)q0r[j] + beta * (T)p0[j], q1 = (T)q1r[j] + beta * (T)p1[j];
+          st2<Tf>(pp + o, (Tf)q0, (Tf)q1);
+          const T c0 = tab[a.n_phase + ph[j].x], c1 = tab[a.n_phase + ph[j].y];
+          acc += c0 * q0 * q0 + c1 * q1 * q1;
+          val = mk<T>(c0 * q0, c1 * q1);
+        }
+        pl[rw[j] * P + col] = val;
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int lr = warp; lr < rb; lr += nwarp) {
+      for (int c2 = lane; c2 < h; c2 += 32) {
+        cx<T> val = mk<T>(0, 0);
+        if (lr < nr) {
+          const long long o = (r0 + lr) * n1 + 2 * c2;
+          if (a.mode == FWD_TAU || a.mode == FWD_STRESS) {
+            Tf v0 = 0, v1 = 0;
+            if (a.in != nullptr) ld2<Tf>(a.in + cbase + o, v0, v1);
+            const uchar2 ph = *reinterpret_cast<const uchar2*>(phase + o);
+            val = mk<T>(w[ph.x] * ((T)v0 + ec), w[ph.y] * ((T)v1 + ec));
+          } else {
+            Tf v0, v1;
+            ld2<Tf>(a.in + cbase + o, v0, v1);
+            val = mk<T>(wc * (T)v0, wc * (T)v1);
+          }
+        }
+        pl[lr * P + c2] = val;
+      }
     }
   }
   __syncthreads();
@@ -178,7 +220,7 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
   if (a.prof != nullptr && tid == 0) {
     const long long vox = (long long)nr * n1;
-    long long fields = (a.mode == INV_CG) ? 5 : 1 + (a.fin == FIN_BASIC);
+    long long fields = (a.mode == INV_CG) ? 2 : 1 + (a.fin == FIN_BASIC);
     long long b = fields * vox * (long long)sizeof(Tf) + (long long)nr * h * (long long)sizeof(cx<T>);
     if (a.b != nullptr) b += vox * (long long)sizeof(double);
     if (a.xsub != nullptr) b += vox * (long long)sizeof(double);
@@ -239,24 +281,36 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
         st2<Tf>(a.out + o, (Tf)v0, (Tf)v1);
       }
     }
-  } else {  // INV_CG: x += alpha p, r -= alpha A p with A p = -eta
-    const long long cbase = (long long)(rhs * 6 + c) * g.M;
+  } else {  // INV_CG: r -= alpha A p with A p = -eta (x += alpha p: next forward pass)
+    // flat index e = row * h + col; kBatch elements' loads in flight before the first store
+    constexpr int kBatch = PlaneCfg<T>::kBatch;
+    const long long cbase = (long long)(rhs * 6 + c) * g.M + r0 * n1;
     const T alpha = (T)a.st[rhs].alpha;
-#pragma unroll 4
-    for (int lr = warp; lr < nr; lr += nwarp) {
-      for (int c2 = lane; c2 < h; c2 += 32) {
-        const long long o = cbase + (r0 + lr) * n1 + 2 * c2;
-        const cx<T> e = pl[lr * P + c2];
-        Tf p0, p1, x0, x1, r_0, r_1;
-        ld2<Tf>(a.p + o, p0, p1);
-        ld2<Tf>(a.x + o, x0, x1);
-        ld2<Tf>(a.r + o, r_0, r_1);
-        const T xa = (T)x0 + alpha * (T)p0, xb = (T)x1 + alpha * (T)p1;
-        const T ra = (T)r_0 + alpha * e.re, rb_ = (T)r_1 + alpha * e.im;
-        st2<Tf>(a.x + o, (Tf)xa, (Tf)xb);
-        st2<Tf>(a.r + o, (Tf)ra, (Tf)rb_);
-        q0 += cw * (ra * ra + rb_ * rb_);
-        q1 += ra * ra + rb_ * rb_;
+    Tf* rp = a.r + cbase;
+    const int total = nr * h;
+    for (int e0 = tid; e0 < total; e0 += kBatch * nthr) {
+      Tf s0[kBatch], s1[kBatch];
+      int rw[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        rw[j] = (int)g.fd_h.div((unsigned)e);
+        if (e < total) {
+          const int o = rw[j] * n1 + 2 * (e - rw[j] * h);
+          ld2<Tf>(rp + o, s0[j], s1[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int e = e0 + j * nthr;
+        if (e < total) {
+          const int col = e - rw[j] * h, o = rw[j] * n1 + 2 * col;
+          const cx<T> v = pl[rw[j] * P + col];
+          const T ra = (T)s0[j] + alpha * v.re, rb_ = (T)s1[j] + alpha * v.im;
+          st2<Tf>(rp + o, (Tf)ra, (Tf)rb_);
+          q0 += cw * (ra * ra + rb_ * rb_);
+          q1 += ra * ra + rb_ * rb_;
+        }
       }
     }
   }
