@@ -125,7 +125,9 @@ typedef struct {
   int32_t status;            /* hom_status of this load */
   int32_t reserved;
   double rel_residual;       /* last relative residual tracked by the iteration */
-  double rel_residual_fp64;  /* ||b - A eps||_L2 / ||b||_L2 recomputed in FP64 at the end */
+  double rel_residual_fp64;  /* ||b - A eps||_L2 / ||b||_L2 of Eq. cg_form recomputed at the end at FP64
+                                accuracy: native FP64 in HOM_FP64, double-float arithmetic (a pair of
+                                floats, about 48 significant bits) in HOM_FP32_REFINE */
 } hom_solve_info;
 
 /* Fills *opt with defaults: HOM_FP32_REFINE, HOM_CG, max_iter 2000, check_every 8,
@@ -138,10 +140,13 @@ HOM_API void hom_default_options(hom_options* opt);
  *              constant along y3 and xi3 = 0: plane strain, or plane stress with the plane-stress
  *              Lame parameter 2 lambda mu / (lambda + 2 mu) in place of lambda).  Planes with
  *              (N1/2) * N2 <= 8192 can use the fused plane kernels; larger ones use split x and y
- *              passes (hom_options.pass_mode).
+ *              passes or cluster plane passes (hom_options.pass_mode).
  *  phase       uint8 [N3][N2][N1], host or device pointer (auto-detected); copied.
  *  n_phase     1..256; every phase index must be < n_phase.
- *  lame        double [n_phase][2] host array of (lambda, mu) per phase; copied.
+ *  lame        double [n_phase][2] host array of (lambda, mu) per phase; copied.  Phases are
+ *              isotropic, like every material of the paper (Sec. 4): the boundary takes no full
+ *              6 x 6 stiffness per phase, and the kernels rely on C being diagonal in the Kelvin
+ *              basis (3K, 2mu).
  *  lambda0,mu0 Lame parameters of the reference medium C0 (mu0 != 0, lambda0+2mu0 != 0).
  *  opt         options (NULL = defaults); the stream pointer is borrowed, not owned.
  *  out         receives the handle (owned by the caller; release with hom_destroy).
