@@ -92,8 +92,12 @@ typedef struct {
                               split; 3 = always cluster for FP32 transforms (fails if no cluster
                               shape fits), split for the FP64-accurate passes */
   int32_t autotune;        /* 1: before the first solve, time one operator application per
-                              candidate launch shape (loads per launch, z-pass tile width) on
-                              this grid and keep the fastest; 0 (default): fixed rules */
+                              candidate launch shape (loads per launch, z stage and tile width,
+                              cluster or split plane passes, y tile width) on this grid and keep
+                              the fastest; 0 (default): fixed rules.  When the environment
+                              variable HOM_TUNE_CACHE names a file, a shape tuned earlier for the
+                              same grid and options is read from it instead of timing again, and a
+                              newly tuned one is appended to it. */
   int32_t polarization_variant; /* HOM_POLARIZATION: 0 = x <- T(x) (Eyre-Milton, Monchiet-Bonnet);
                               1 = x <- (x + T(x)) / 2 (the averaged, augmented-Lagrangian form,
                               which also converges where a phase modulus is 0) */

@@ -15,6 +15,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "lib", "libhom.so")
+# launch shapes tuned with the kernels of one build (hom_options.autotune with HOM_TUNE_CACHE)
+TUNE_CACHE = os.path.join(PKG, "lib", "tune_cache.txt")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
@@ -68,6 +70,8 @@ def build(force=False, verbose=False, extra=None):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
+    if os.path.exists(TUNE_CACHE):   # shapes tuned for the previous kernels
+        os.remove(TUNE_CACHE)
     return LIB
 
 

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <string>
@@ -594,8 +595,60 @@ hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<i
 // of at least 32 bytes per z-plane) and, on planes above one CTA, the cluster plane passes against
 // the split x and y passes; then the split y pass's tile width.  It tunes the passes of the
 // iteration precision T.
+// Tuning cache (HOM_TUNE_CACHE): one line per tuned handle kind,
+//   key: n1 n2 n3 precision transform-bytes z_mode pass_mode n_rve green chunk-capacity
+//   value: chunk zc_off zc_lg ztile_lg pc_off ty_log2
+// The last line with a matching key wins.  A shape read back is one the tuner itself produced for
+// the same grid and options, so it is valid for this handle.
+std::string tune_key(const hom_ctx* c, size_t tbytes) {
+  char b[192];
+  std::snprintf(b, sizeof(b), "%d %d %d %d %zu %d %d %d %d %d", c->g.n1, c->g.n2, c->g.n3, c->opt.precision, tbytes,
+                c->opt.z_mode, c->opt.pass_mode, c->n_rve, c->opt.green_operator, c->chunk);
+  return b;
+}
+
+bool tune_cache_load(hom_ctx* c, const char* path, const std::string& key, int idx) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool hit = false;
+  int v[6] = {0, 0, 0, 0, 0, 0};
+  while (std::fgets(line, sizeof(line), f)) {
+    const char* bar = std::strchr(line, '|');
+    if (!bar || std::string(line, (size_t)(bar - line)) != key + " ") continue;
+    int w[6];
+    if (std::sscanf(bar + 1, "%d %d %d %d %d %d", &w[0], &w[1], &w[2], &w[3], &w[4], &w[5]) == 6) {
+      std::memcpy(v, w, sizeof(v));
+      hit = true;
+    }
+  }
+  std::fclose(f);
+  if (!hit || v[0] < 1 || v[0] > c->chunk || v[5] < 0 || v[5] > 4 || (c->g.split && !ytile_fits(c->g, v[5]))) return false;
+  c->chunk = v[0];
+  c->zc_off[idx] = v[1] != 0;
+  c->zc_lg[idx] = v[2];
+  c->ztile_lg[idx] = v[3];
+  c->pc_off = v[4] != 0;
+  if (c->g.split) set_ytile(c->g, v[5]);
+  return true;
+}
+
+void tune_cache_store(const hom_ctx* c, const char* path, const std::string& key, int idx) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s | %d %d %d %d %d %d\n", key.c_str(), c->chunk, c->zc_off[idx] ? 1 : 0, c->zc_lg[idx],
+               c->ztile_lg[idx], c->pc_off ? 1 : 0, c->g.ty_log2);
+  std::fclose(f);
+}
+
 template <typename T>
 hom_status autotune(hom_ctx* c) {
+  const char* cache = std::getenv("HOM_TUNE_CACHE");
+  const std::string key = tune_key(c, sizeof(T));
+  if (cache && *cache && tune_cache_load(c, cache, key, sizeof(T) == 8 ? 1 : 0)) {
+    c->tuned = true;
+    return HOM_OK;
+  }
   const int nt = std::min(c->chunk, 12);
   std::vector<int> chunks;
   for (int k : {1, 2, 3, 4, 6, 8, 12})
@@ -694,6 +747,7 @@ hom_status autotune(hom_ctx* c) {
   c->ev_pool.push_back(e0);
   c->ev_pool.push_back(e1);
   c->tuned = true;
+  if (cache && *cache) tune_cache_store(c, cache, key, idx);
   return HOM_OK;
 }
 

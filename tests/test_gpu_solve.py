@@ -199,3 +199,23 @@ def test_fp32_mode_residual_certified_at_1e10():
         assert res < 1e-10, (a, res)
         assert abs(res - info[k]["rel_residual_fp64"]) < 0.05 * res + 1e-13, (res, info[k])
     H.close()
+
+
+def test_tuning_cache_reuses_the_tuned_shape(tmp_path, monkeypatch):
+    """With HOM_TUNE_CACHE set, the first autotuned handle of a grid writes its launch shape and a
+    second handle of the same grid and options reads it back instead of timing again."""
+    from paper_1712_05145_gb300 import hom
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("HOM_TUNE_CACHE", str(path))
+    ms = synthetic.random_spheres((32, 32, 32), seed=12)
+    shapes, effs = [], []
+    for _ in range(2):
+        H = hom.Homogenization(ms, precision=hom.HOM_FP32_REFINE, autotune=1)
+        H.solve(0, 1e-7)
+        shapes.append((hom.hom_launch_config(H.h), hom.hom_zpass_config(H.h), hom.hom_plane_config(H.h)))
+        effs.append(H.effective(0))
+        H.close()
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and "|" in lines[0]
+    assert shapes[0] == shapes[1]
+    assert np.array_equal(effs[0], effs[1])
