@@ -109,6 +109,12 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
 }
 
+// The same where the range allows it (16-byte aligned start and size); otherwise nothing.
+__device__ __forceinline__ void prefetch_l2_if_aligned(const void* ptr, unsigned bytes) {
+  if (bytes != 0 && (bytes & 15u) == 0 && (reinterpret_cast<unsigned long long>(ptr) & 15ull) == 0)
+    prefetch_l2(ptr, bytes);
+}
+
 // Publishes this block's NQ totals (valid in thread 0 after block_sum_f64) and lets the
 // block that draws the last ticket sum all ncta partials in a fixed order.  Returns
 // true in that block, with the grand totals in thread 0's v.

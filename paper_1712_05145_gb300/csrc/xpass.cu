@@ -30,6 +30,23 @@ __global__ void __launch_bounds__(256) xpass_fwd_kernel(const FwdArgs<Tf, T> a) 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
 
+  if (tid == 0) {
+    // this block's rows are contiguous in every field: their reads start into L2 now, while the
+    // tables load (one bulk prefetch per field)
+    const long long cb = (long long)(rhs * a.in_ncomp + c) * g.M + r0 * n1;
+    const unsigned fb = (unsigned)((long long)nr * n1 * (long long)sizeof(Tf));
+    if (a.mode == FWD_CG) {
+      prefetch_l2_if_aligned(a.r + cb, fb);
+      if (a.st[rhs].restart == 0) {
+        prefetch_l2_if_aligned(a.p + cb, fb);
+        prefetch_l2_if_aligned(a.x + cb, fb);
+      }
+    } else if (a.in != nullptr) {
+      prefetch_l2_if_aligned(a.in + cb, fb);
+    }
+    if (a.mode != FWD_COPY && a.mode != FWD_C0)
+      prefetch_l2_if_aligned(a.phase + (long long)rve_of(rhs, a.rve_loads) * g.M + r0 * n1, (unsigned)(nr * n1));
+  }
   for (int i = tid; i < h; i += nthr) twh[i] = ldg_cx(a.tw_h + i);
   for (int i = tid; i <= h; i += nthr) tw1[i] = ldg_cx(a.tw_n1 + i);
   const int rve = rve_of(rhs, a.rve_loads);
@@ -203,6 +220,19 @@ __global__ void __launch_bounds__(256) xpass_inv_kernel(const InvArgs<Tf, T> a) 
   int* flag = reinterpret_cast<int*>(sh + 64);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  if (tid == 0) {
+    // the epilogue's field rows (contiguous) start into L2 while the transforms run
+    const unsigned fb = (unsigned)((long long)nr * n1 * (long long)sizeof(Tf));
+    if (a.mode == INV_CG) {
+      prefetch_l2_if_aligned(a.r + (long long)(rhs * 6 + c) * g.M + r0 * n1, fb);
+    } else {
+      const long long cb = (long long)(rhs * a.out_ncomp + c) * g.M + r0 * n1;
+      const unsigned db = (unsigned)((long long)nr * n1 * (long long)sizeof(double));
+      if (a.b != nullptr) prefetch_l2_if_aligned(a.b + cb, db);
+      if (a.xsub != nullptr) prefetch_l2_if_aligned(a.xsub + cb, db);
+      if (a.fin == FIN_BASIC && a.prev != nullptr) prefetch_l2_if_aligned(a.prev + cb, fb);
+    }
+  }
   // the block's spectrum rows go to shared memory by cp.async while the twiddle tables load
   const cx<T>* Sc = a.S + (long long)(lrhs * a.s_ncomp + c) * g.n3 * g.plane_c;
 #pragma unroll 4

@@ -29,6 +29,26 @@ constexpr size_t kZcMaxSmem = 80 * 1024;
 template <typename T> struct ZcCfg { static constexpr int kMinBlocks = 1; };
 template <> struct ZcCfg<float> { static constexpr int kMinBlocks = 2; };
 
+// -Gamma0_hat(xi) : tau_hat at tile element q (column f0 + q mod 2^lg, z-plane q / 2^lg), in place on
+// its six Kelvin components k; columns past the plane are left as they are
+template <typename T>
+__device__ __forceinline__ void contract_point(const Geo& g, const ZArgs<T>& a, long long f0, int lg, int n3, int q,
+                                               cx<T>* k, T c1, T c2h, T scale, long long nmain) {
+  const int tc = q & ((1 << lg) - 1), n = q >> lg;
+  const long long f = f0 + tc;
+  if (f >= g.plane_c) return;
+  int kx, ky;
+  if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
+  else { ky = (int)(f - nmain); kx = g.h; }
+  // discrete wave vector (Nyquist components taken as 0), or the rotated difference symbol
+  T x1, x2, x3;
+  wave_vector<T>(g, a.green, a.gtab, kx, ky, n, x1, x2, x3);
+  cx<T> tt[6], w1, w2, w3;
+  kelvin_to_tensor<T>(k, tt);
+  tensor_dot_xi<T>(tt, x1, x2, x3, w1, w2, w3);
+  green_from_w<T>(k, w1, w2, w3, x1, x2, x3, c1, c2h, scale);
+}
+
 template <typename T, int EPT>
 __global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>::kMinBlocks) zcluster_kernel(const ZArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -74,21 +94,10 @@ __global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>
     const int share = (per + kZcComps - 1) / kZcComps;
     const int q0 = comp * share, q1 = (q0 + share < per) ? q0 + share : per;
     for (int q = q0 + tid; q < q1; q += nthr) {
-      const int tc = q & (TC - 1), n = q >> lg;
-      const long long f = f0 + tc;
-      if (f >= g.plane_c) continue;
-      int kx, ky;
-      if (f < nmain) { ky = (int)g.fd_h.div((unsigned)f); kx = (int)f - ky * g.h; }
-      else { ky = (int)(f - nmain); kx = g.h; }
-      // discrete wave vector (Nyquist components taken as 0), or the rotated difference symbol
-      T x1, x2, x3;
-      wave_vector<T>(g, a.green, a.gtab, kx, ky, n, x1, x2, x3);
-      cx<T> k[6], tt[6], w1, w2, w3;
+      cx<T> k[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) k[i] = part[i][q];
-      kelvin_to_tensor<T>(k, tt);
-      tensor_dot_xi<T>(tt, x1, x2, x3, w1, w2, w3);
-      green_from_w<T>(k, w1, w2, w3, x1, x2, x3, c1, c2h, scale);
+      contract_point<T>(g, a, f0, lg, n3, q, k, c1, c2h, scale, nmain);
 #pragma unroll
       for (int i = 0; i < 6; ++i) part[i][q] = k[i];
     }
