@@ -163,8 +163,11 @@ def test_zero_load_is_exact_and_free(precision, scheme):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotuned_launch_shape_gives_identical_results(precision):
-    """The autotuner only changes loads per launch and z-pass tile width; per-load reductions keep
-    their order, so the solution is the same bits."""
+    """The autotuner changes loads per launch, tile widths and which z-stage kernel runs.  Loads
+    per launch and tile widths keep every per-load reduction in its order, so with the same z
+    kernel the solution is the same bits; a different z kernel (cluster or single CTA) computes the
+    same contraction in another compiled kernel, so there the results agree within the parity
+    tolerance."""
     from paper_1712_05145_gb300 import hom
     ms = synthetic.random_spheres((32, 32, 32), seed=12)
     out = []
@@ -179,10 +182,13 @@ def test_autotuned_launch_shape_gives_identical_results(precision):
             assert (cluster == 0 and lg >= 0) or (cluster == 1 and zlg >= 0)
         else:
             assert lg == -1 and cluster == 1
-        out.append((H.effective(0), H.field(0, 2), [i["iterations"] for i in info]))
+        out.append((H.effective(0), H.field(0, 2), cluster))
         H.close()
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-    assert out[0][2] == out[1][2]
+    if out[0][2] == out[1][2]:
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    else:
+        assert rel_err(out[1][0], out[0][0]) < TOL_EFF[precision]
+        assert rel_err(out[1][1], out[0][1]) < TOL[precision]
 
 
 def test_fp32_mode_residual_certified_at_1e10():
