@@ -103,8 +103,13 @@ typedef struct {
                               which also converges where a phase modulus is 0) */
   int32_t z_mode;          /* z stage of the LS step: 0 = cluster z pass (six CTAs, one per Kelvin
                               component, meeting in distributed shared memory for the Green
-                              contraction) where its tile fits, else the single-CTA z pass;
-                              1 = always the single-CTA z pass (three passes on deep grids) */
+                              contraction) where its tile fits, else the single-CTA z pass (the
+                              autotuner may pick any of the three forms);
+                              1 = always the single-CTA z pass (three passes on deep grids);
+                              2 = the cluster z pass with its tiles moved by TMA tensor loads and
+                              stores where that fits (FP32 transforms, N3 >= 16, an even number of
+                              spectrum columns per plane), else as 0.  Results are identical to
+                              those of 0 with the same tile width. */
   int32_t green_operator;  /* HOM_GREEN_SPECTRAL (0): Gamma0_hat of Sec. 2 at the discrete wave
                               vector (Nyquist components 0).  HOM_GREEN_ROTATED (1): the Green
                               operator of the rotated finite-difference discretisation (corner
@@ -377,8 +382,9 @@ HOM_API hom_status hom_launch_config(hom_t h, int32_t* loads_per_launch, int32_t
  * passes (hom_options.pass_mode), 0 when the fused plane kernels or the split x and y passes run. */
 HOM_API hom_status hom_plane_config(hom_t h, int32_t* cluster_ctas);
 
-/* z stage of the handle's iteration passes: *cluster = 1 for the cluster z pass (hom_options.z_mode),
- * *tile_log2 its tile width as log2 of its columns (-1: the default rule).  Pointers nullable. */
+/* z stage of the handle's iteration passes: *cluster = 1 for the cluster z pass, 2 for its TMA
+ * form, 0 for the single-CTA z pass (hom_options.z_mode); *tile_log2 its tile width as log2 of its
+ * columns (-1: the default rule).  Pointers nullable. */
 HOM_API hom_status hom_zpass_config(hom_t h, int32_t* cluster, int32_t* tile_log2);
 
 /* Kernels this library has launched in this process so far, over all handles, servers and the

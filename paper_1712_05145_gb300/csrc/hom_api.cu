@@ -111,6 +111,8 @@ struct hom_ctx {
   int ztile_lg[2] = {-1, -1};  // z-pass tile width forced by the autotuner (FP32, FP64); -1: rule
   int zc_lg[2] = {-1, -1};     // cluster z-pass tile width forced by the autotuner; -1: rule
   bool zc_off[2] = {false, false};  // the autotuner found the single-CTA z pass faster
+  bool zc_tma = false;         // FP32 cluster z pass: the TMA variant (z_mode 2, or the autotuner's pick)
+  unsigned* d_kerr = nullptr;  // bits set by kernels whose bounded waits gave up
   bool pc_off = false;         // the autotuner found the split x and y passes faster than the cluster ones
   bool tuned = false;
   void* d_bicg = nullptr;    // BiCGSTAB fields r_hat, v, s, t (the polarization scheme: eta)
@@ -283,6 +285,7 @@ ZArgs<T> z_args(hom_ctx* c, int mode, int nin, int nout) {
   a.tw_n3 = tw<T>(c, 3);
   a.green = c->opt.green_operator;
   a.gtab = c->d_gtab;
+  a.err = c->d_kerr;
   zpass_tiling<T>(a, c->ztile_lg[sizeof(T) == 8 ? 1 : 0]);
   return a;
 }
@@ -432,10 +435,17 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArg
     CKS(fwd_xy<Tf1, T>(c, fa, n));
     ZArgs<T> zc = za;
     const int zi = sizeof(T) == 8 ? 1 : 0;
-    if (za.mode == Z_GAMMA && za.ncomp_in == 6 && za.ncomp_out == 6 && c->opt.z_mode == 0 && !c->zc_off[zi] &&
+    if (za.mode == Z_GAMMA && za.ncomp_in == 6 && za.ncomp_out == 6 && c->opt.z_mode != 1 && !c->zc_off[zi] &&
         zcluster_tiling<T>(zc, c->zc_lg[zi])) {
       // one pass: six CTAs per tile, the contraction in distributed shared memory
-      CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zcluster<T>(zc, n, c->stream); }));
+      bool tma = false;
+      if constexpr (std::is_same<T, float>::value) tma = c->zc_tma && ztma_fits(c->g, zc.tc_log2);
+      if (tma) {
+        if constexpr (std::is_same<T, float>::value)
+          CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zcluster_tma(zc, n, c->stream); }));
+      } else {
+        CKS(timed_launch(c, kind_of<T>(HOM_KERNEL_ZPASS), [&] { return launch_zcluster<T>(zc, n, c->stream); }));
+      }
     } else if (za.mode == Z_GAMMA && za.ncomp_in == 6 && ((size_t)1 << za.tc_log2) * sizeof(cx<T>) < 32) {
       // deep grid: the fused z tiles would be narrower than a sector; split the z stage into
       // per-component z FFTs (one "load" per component, all loads of the chunk processed) and
@@ -456,11 +466,22 @@ hom_status ls_pass(hom_ctx* c, int nrhs, FwdArgs<Tf1, T> fa, ZArgs<T> za, InvArg
   return HOM_OK;
 }
 
+// Reads the kernels' error word (bits of bounded waits that gave up) and clears it.
+hom_status check_kernel_flags(hom_ctx* c) {
+  if (!c->d_kerr) return HOM_OK;
+  unsigned f = 0;
+  CK(cudaMemcpyAsync(&f, c->d_kerr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (f == 0) return HOM_OK;
+  CK(cudaMemsetAsync(c->d_kerr, 0, sizeof(unsigned), c->stream));
+  return fail(c, HOM_ERR_CUDA, "a kernel gave up a bounded wait (flags 0x%x): its results are invalid", f);
+}
+
 hom_status read_states(hom_ctx* c, int n, std::vector<RhsState>& h) {
   h.resize(n);
   CK(cudaMemcpyAsync(h.data(), c->d_st, sizeof(RhsState) * n, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  return HOM_OK;
+  return check_kernel_flags(c);
 }
 hom_status write_states(hom_ctx* c, const std::vector<RhsState>& h) {
   CK(cudaMemcpyAsync(c->d_st, h.data(), sizeof(RhsState) * h.size(), cudaMemcpyHostToDevice, c->stream));
@@ -597,7 +618,7 @@ hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<i
 // iteration precision T.
 // Tuning cache (HOM_TUNE_CACHE): one line per tuned handle kind,
 //   key: n1 n2 n3 precision transform-bytes z_mode pass_mode n_rve green chunk-capacity
-//   value: chunk zc_off zc_lg ztile_lg pc_off ty_log2
+//   value: chunk zc_off zc_lg ztile_lg pc_off ty_log2 zc_tma
 // The last line with a matching key wins.  A shape read back is one the tuner itself produced for
 // the same grid and options, so it is valid for this handle.
 std::string tune_key(const hom_ctx* c, size_t tbytes) {
@@ -612,12 +633,12 @@ bool tune_cache_load(hom_ctx* c, const char* path, const std::string& key, int i
   if (!f) return false;
   char line[512];
   bool hit = false;
-  int v[6] = {0, 0, 0, 0, 0, 0};
+  int v[7] = {0, 0, 0, 0, 0, 0, 0};
   while (std::fgets(line, sizeof(line), f)) {
     const char* bar = std::strchr(line, '|');
     if (!bar || std::string(line, (size_t)(bar - line)) != key + " ") continue;
-    int w[6];
-    if (std::sscanf(bar + 1, "%d %d %d %d %d %d", &w[0], &w[1], &w[2], &w[3], &w[4], &w[5]) == 6) {
+    int w[7];
+    if (std::sscanf(bar + 1, "%d %d %d %d %d %d %d", &w[0], &w[1], &w[2], &w[3], &w[4], &w[5], &w[6]) == 7) {
       std::memcpy(v, w, sizeof(v));
       hit = true;
     }
@@ -630,14 +651,15 @@ bool tune_cache_load(hom_ctx* c, const char* path, const std::string& key, int i
   c->ztile_lg[idx] = v[3];
   c->pc_off = v[4] != 0;
   if (c->g.split) set_ytile(c->g, v[5]);
+  if (idx == 0) c->zc_tma = v[6] != 0;
   return true;
 }
 
 void tune_cache_store(const hom_ctx* c, const char* path, const std::string& key, int idx) {
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s | %d %d %d %d %d %d\n", key.c_str(), c->chunk, c->zc_off[idx] ? 1 : 0, c->zc_lg[idx],
-               c->ztile_lg[idx], c->pc_off ? 1 : 0, c->g.ty_log2);
+  std::fprintf(f, "%s | %d %d %d %d %d %d %d\n", key.c_str(), c->chunk, c->zc_off[idx] ? 1 : 0, c->zc_lg[idx],
+               c->ztile_lg[idx], c->pc_off ? 1 : 0, c->g.ty_log2, c->zc_tma ? 1 : 0);
   std::fclose(f);
 }
 
@@ -653,18 +675,23 @@ hom_status autotune(hom_ctx* c) {
   std::vector<int> chunks;
   for (int k : {1, 2, 3, 4, 6, 8, 12})
     if (k <= nt) chunks.push_back(k);
-  // z-stage candidates: (0, lg) the single-CTA z pass with 2^lg columns, (1, lg) the cluster z pass
-  std::vector<std::pair<int, int>> zcand;
+  // z-stage candidates: (0, lg) the single-CTA z pass with 2^lg columns, (1, lg) the cluster z
+  // pass, (2, lg) its TMA variant (FP32 transforms).  z_mode 2 keeps the TMA variant where it fits.
+  std::vector<std::pair<int, int>> zcand, ztma;
   for (int lg = 0; lg <= 4; ++lg)
     if (zpass_tile_fits(c->g, sizeof(cx<T>), 6, lg)) zcand.push_back({0, lg});
-  if (c->opt.z_mode == 0) {
+  if (c->opt.z_mode != 1) {
     for (int lg = 0; lg <= 6; ++lg) {
       ZArgs<T> probe{};
       probe.g = c->g;
-      if (((size_t)1 << lg) * sizeof(cx<T>) >= 32 && zcluster_tiling<T>(probe, lg) && probe.tc_log2 == lg)
-        zcand.push_back({1, lg});
+      if (((size_t)1 << lg) * sizeof(cx<T>) >= 32 && zcluster_tiling<T>(probe, lg) && probe.tc_log2 == lg) {
+        if (c->opt.z_mode == 0) zcand.push_back({1, lg});
+        if (std::is_same<T, float>::value && ztma_fits(c->g, lg)) ztma.push_back({2, lg});
+      }
     }
   }
+  if (c->opt.z_mode == 2 && !ztma.empty()) zcand = ztma;
+  else zcand.insert(zcand.end(), ztma.begin(), ztma.end());
   if (zcand.empty()) return HOM_OK;
   const size_t fb = tbytes<T>(c, nt, 6);
   void *vin, *vout;
@@ -693,6 +720,7 @@ hom_status autotune(hom_ctx* c) {
       c->pc_off = pc_off;
       c->chunk = ck;
       c->zc_off[idx] = (zk.first == 0);
+      if (std::is_same<T, float>::value) c->zc_tma = (zk.first == 2);
       if (zk.first == 0) c->ztile_lg[idx] = lg;
       else c->zc_lg[idx] = lg;
       CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));  // warm-up
@@ -715,6 +743,7 @@ hom_status autotune(hom_ctx* c) {
   c->pc_off = best_pc_off;
   c->chunk = best_chunk;
   c->zc_off[idx] = (best_kind == 0);
+  if (std::is_same<T, float>::value) c->zc_tma = (best_kind == 2);
   if (best_kind == 0) {
     c->ztile_lg[idx] = best_lg;
     c->zc_lg[idx] = -1;
@@ -1611,9 +1640,10 @@ HOM_API hom_status hom_zpass_config(hom_t c, int32_t* cluster, int32_t* tile_log
   ZArgs<double> p64{};
   p32.g = c->g;
   p64.g = c->g;
-  bool on = c->opt.z_mode == 0 && !c->zc_off[zi];
+  bool on = c->opt.z_mode != 1 && !c->zc_off[zi];
   if (on) on = c->fp32 ? zcluster_tiling<float>(p32, c->zc_lg[zi]) : zcluster_tiling<double>(p64, c->zc_lg[zi]);
-  if (cluster) *cluster = on ? 1 : 0;
+  const bool tma = on && c->fp32 && c->zc_tma && ztma_fits(c->g, p32.tc_log2);
+  if (cluster) *cluster = tma ? 2 : (on ? 1 : 0);
   if (tile_log2) *tile_log2 = on ? (c->fp32 ? p32.tc_log2 : p64.tc_log2) : c->ztile_lg[zi];
   return HOM_OK;
 }
@@ -1762,7 +1792,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     return HOM_ERR_SIZE;
   const int pass_mode = opt ? opt->pass_mode : 0;
   if (pass_mode < 0 || pass_mode > 3) return HOM_ERR_ARG;
-  if (opt && (opt->z_mode < 0 || opt->z_mode > 1)) return HOM_ERR_ARG;
+  if (opt && (opt->z_mode < 0 || opt->z_mode > 2)) return HOM_ERR_ARG;
   if (opt && opt->green_operator != HOM_GREEN_SPECTRAL && opt->green_operator != HOM_GREEN_ROTATED) return HOM_ERR_ARG;
   if (pass_mode == 1 && (long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
 
@@ -1903,6 +1933,9 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     if ((s = dalloc(c, (void**)&c->d_S64, b64 / 6 * c->S64_comps)) != HOM_OK) return bail(s);
   }
   if ((s = ensure_cap(c, 6)) != HOM_OK) return bail(s);
+  if ((s = dalloc(c, (void**)&c->d_kerr, sizeof(unsigned))) != HOM_OK) return bail(s);
+  if (cudaMemsetAsync(c->d_kerr, 0, sizeof(unsigned), c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
+  c->zc_tma = (c->opt.z_mode == 2);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
   *out = c;
   return HOM_OK;
@@ -2075,7 +2108,7 @@ HOM_API hom_status hom_ls_apply(hom_t c, int32_t nrhs, const double* eps_in, con
     CK(launch_kelvin_to_mandel<double>((const double*)vout, eps_out, c->g.M, nrhs, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
-  return HOM_OK;
+  return check_kernel_flags(c);
 }
 
 }  // extern "C"

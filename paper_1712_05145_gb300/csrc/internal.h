@@ -121,6 +121,8 @@ struct ZArgs {
   const double* gtab;    // green == 1: sin, cos of pi j / N per axis (see wave_vector)
   unsigned long long* prof;
   const cx<T>* tw_n3;
+  unsigned* err;         // nullable: bits set by kernels whose bounded waits gave up (1) or whose
+                         // shared-memory layout was unusable (2)
 };
 
 template <typename Tf, typename T>

@@ -16,6 +16,7 @@
 
 #include "ls_common.cuh"
 #include "spectral.cuh"
+#include "tma.cuh"
 #include "zcluster.h"
 
 namespace cg = cooperative_groups;
@@ -112,6 +113,86 @@ __global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>
   }
 }
 
+// ---- TMA variant (FP32) ------------------------------------------------------------------------
+// The same tile work with the tile moved by the tensor-memory accelerator: thread 0 issues the
+// tensor loads of the CTA's component (one box per 256 z-planes), which complete on an mbarrier,
+// and after the inverse FFTs the tensor stores.  Columns past the plane read as zero and are not
+// written.  Several CTAs per SM overlap one tile's copies with other tiles' FFTs.  (A persistent
+// form that loops over tiles measured worse at compile time already: the FFT stages' thread-
+// invariant indexes of every length stay live across the loop and spill.)
+constexpr unsigned long long kZtWaitNs = 2000000000ull;  // a tile load that takes 2 s is an error
+
+template <int EPT>
+__global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, 2)
+    zcluster_tma_kernel(const __grid_constant__ CUtensorMap tm, const ZArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char zt_smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const Geo& g = a.g;
+  const int comp = (int)cl.block_rank();
+  const int tile = blockIdx.x / kZcComps, lrhs = blockIdx.y, rhs = a.rhs0 + lrhs;
+  if (a.st != nullptr && a.st[rhs].active == 0) return;   // the whole cluster leaves together
+  const int tid = threadIdx.x;
+  // tensor copies need 128-byte aligned shared addresses; every CTA has the same layout, so on a
+  // misaligned base all CTAs leave here, before any cluster barrier
+  if ((smem_u32(zt_smem) & 127u) != 0) {
+    if (tid == 0 && a.err != nullptr) atomicOr(a.err, 2u);
+    return;
+  }
+  const int lg = a.tc_log2, TC = 1 << lg, n3 = g.n3, per = n3 * TC;
+  const int nbox = (n3 + 255) / 256, rows = n3 / nbox;   // a box spans at most 256 z-planes
+  const int zc = lrhs * kZcComps + comp;                  // this CTA's component plane in the tensor
+  cx<float>* buf = reinterpret_cast<cx<float>*>(zt_smem);   // [n3][TC]
+  cx<float>* twz = buf + per;
+  const uint32_t bar = smem_u32(twz + n3), sbuf = smem_u32(buf);
+  const uint32_t box_bytes = (uint32_t)rows * TC * (uint32_t)sizeof(cx<float>);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, (uint32_t)nbox * box_bytes);
+    for (int b = 0; b < nbox; ++b) tma_load_3d(sbuf + b * box_bytes, &tm, tile * TC, b * rows, zc, bar);
+  }
+  for (int i = tid; i < n3; i += blockDim.x) twz[i] = ldg_cx(a.tw_n3 + i);
+  __syncthreads();   // the mbarrier is initialised before anyone waits on it
+  const bool ok = mbar_wait_bounded(bar, 0, kZtWaitNs);
+  fft_pencils<float, -1, EPT>(buf, ColAddr{TC}, n3, TC, a.fd_in, twz);
+  cl.sync();   // every component of the tile is transformed along z
+  {
+    cx<float>* part[kZcComps];
+#pragma unroll
+    for (int r = 0; r < kZcComps; ++r) part[r] = cl.map_shared_rank(buf, r);
+    float c1, c2h;
+    green_consts<float>(a.c0, rve_of(rhs, a.rve_loads), a.lam0, a.mu0, c1, c2h);
+    const float scale = (float)a.scale;
+    const long long nmain = (long long)g.n2 * g.h, f0 = (long long)tile * TC;
+    const int share = (per + kZcComps - 1) / kZcComps;
+    const int q0 = comp * share, q1 = (q0 + share < per) ? q0 + share : per;
+    for (int q = q0 + tid; q < q1; q += blockDim.x) {
+      cx<float> k[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) k[i] = part[i][q];
+      contract_point<float>(g, a, f0, lg, n3, q, k, c1, c2h, scale, nmain);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) part[i][q] = k[i];
+    }
+  }
+  cl.sync();   // no CTA touches another's buffer after this
+  fft_pencils<float, +1, EPT>(buf, ColAddr{TC}, n3, TC, a.fd_in, twz);
+  fence_proxy_async_smem();   // the inverse FFT's shared-memory writes, before the tensor store reads them
+  __syncthreads();
+  if (tid == 0) {
+    for (int b = 0; b < nbox; ++b) tma_store_3d(&tm, tile * TC, b * rows, zc, sbuf + b * box_bytes);
+    bulk_commit();
+    if (a.prof != nullptr) {
+      const long long f0 = (long long)tile * TC;
+      const long long cols = (g.plane_c - f0 < TC) ? g.plane_c - f0 : TC;
+      atomicAdd(a.prof, (unsigned long long)(2LL * n3 * cols * (long long)sizeof(cx<float>)));
+      if (comp == 0) atomicAdd(a.prof + 1, (unsigned long long)(n3 * cols));
+    }
+    bulk_wait_all();   // the stores have finished before the CTA's shared memory is released
+  }
+  if (!ok && a.err != nullptr) atomicOr(a.err, 1u);
+}
+
 static size_t zcluster_smem(const Geo& g, size_t elem, int lg) {
   return ((size_t)g.n3 * ((size_t)1 << lg) + g.n3) * elem;
 }
@@ -169,5 +250,60 @@ cudaError_t launch_zcluster(const ZArgs<T>& a, int nrhs, cudaStream_t s) {
 template cudaError_t launch_zcluster<float>(const ZArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_zcluster<double>(const ZArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_zcluster<df64>(const ZArgs<df64>&, int, cudaStream_t);
+
+// ---- TMA variant: host side ----------------------------------------------------------------
+bool ztma_fits(const Geo& g, int lg) {
+  // the plain cluster tile limits, whole 16-byte box rows (2 columns at least) and 16-byte tensor
+  // strides (an even number of spectrum columns per plane)
+  return lg >= 1 && g.n3 >= 16 && zcluster_tile_fits(g, sizeof(cx<float>), lg) && (g.plane_c % 2) == 0;
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// the driver's tensor-map encoder, found through the runtime (no link against the driver library)
+EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiled) nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+}  // namespace
+
+cudaError_t launch_zcluster_tma(const ZArgs<float>& a, int nrhs, cudaStream_t s) {
+  const Geo& g = a.g;
+  const long long per = (long long)g.n3 << a.tc_log2;
+  if (a.mode != Z_GAMMA || a.ncomp_in != 6 || a.ncomp_out != 6 || !ztma_fits(g, a.tc_log2) || nrhs < 1 ||
+      per > (long long)kEPT * a.nthr || a.nthr > 512 || a.ntiles < 1 ||
+      (reinterpret_cast<uintptr_t>(a.S) & 15) != 0)
+    return cudaErrorInvalidValue;
+  const EncodeTiled enc = encode_tiled();
+  if (enc == nullptr) return cudaErrorNotSupported;
+  const int nbox = (g.n3 + 255) / 256, rows = g.n3 / nbox;
+  const size_t elem = sizeof(cx<float>);
+  // the spectra of the launch's loads: [6 nrhs component planes][n3][plane_c] 8-byte elements
+  CUtensorMap tm;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.plane_c, (cuuint64_t)g.n3, (cuuint64_t)kZcComps * (cuuint64_t)nrhs};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.plane_c * elem, (cuuint64_t)g.n3 * (cuuint64_t)g.plane_c * elem};
+  const cuuint32_t box[3] = {(cuuint32_t)1 << a.tc_log2, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)a.S, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const size_t smem = (size_t)(per + g.n3) * elem + 16;
+  auto k = zcluster_tma_kernel<kEPT>;
+  cudaError_t err = set_smem(k, smem);
+  if (err != cudaSuccess) return err;
+  dim3 grid((unsigned)(a.ntiles * kZcComps), (unsigned)nrhs);
+  count_launch();
+  k<<<grid, a.nthr, smem, s>>>(tm, a);
+  return cudaGetLastError();
+}
 
 }  // namespace hom

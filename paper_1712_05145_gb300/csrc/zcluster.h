@@ -21,4 +21,11 @@ bool zcluster_tile_fits(const Geo& g, size_t elem, int lg);
 template <typename T>
 cudaError_t launch_zcluster(const ZArgs<T>& a, int nrhs, cudaStream_t s);
 
+// The TMA variant (FP32): the same tile work, with each CTA's tile loaded by TMA tensor loads that
+// complete on an mbarrier and written back by TMA tensor stores.  ztma_fits: whether tiles of 2^lg
+// columns can run it on this grid (tiling from zcluster_tiling with that width).  Its bounded wait
+// sets bits in a.err when it gives up.
+bool ztma_fits(const Geo& g, int lg);
+cudaError_t launch_zcluster_tma(const ZArgs<float>& a, int nrhs, cudaStream_t s);
+
 }  // namespace hom

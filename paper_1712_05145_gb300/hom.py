@@ -417,7 +417,8 @@ def hom_plane_config(h):
 
 
 def hom_zpass_config(h):
-    """(1 if the cluster z pass runs else 0, its tile log2 width or -1) of a handle's iteration passes."""
+    """(z stage, tile log2 width or -1) of a handle's iteration passes; the z stage is 1 for the
+    cluster z pass, 2 for its TMA form, 0 for the single-CTA z pass."""
     a, b = ctypes.c_int32(), ctypes.c_int32()
     _check(h, load_library().hom_zpass_config(h, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
