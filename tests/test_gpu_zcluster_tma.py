@@ -31,9 +31,9 @@ def _config(H):
 
 
 # (grid, expected z stage): plane_c = n2 (n1/2 + 1); N3 = 384 and 512 take two boxes of 192 / 256
-# z-planes; 260, 90 and 108 spectrum columns leave a ragged last tile of the default width (16
+# z-planes; 312, 54 and 108 spectrum columns leave a ragged last tile of the default width (16
 # columns at N3 = 384 and 512, 64 at N3 = 64); 15 columns (odd) rule the TMA form out
-GRIDS = [((24, 20, 384), 2), ((16, 10, 512), 2), ((16, 12, 64), 2), ((8, 3, 32), 1)]
+GRIDS = [((24, 24, 384), 2), ((16, 6, 512), 2), ((16, 12, 64), 2), ((8, 3, 32), 1)]
 
 
 @pytest.mark.parametrize("grid,kind", GRIDS, ids=["x".join(map(str, g[0])) for g in GRIDS])
