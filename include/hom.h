@@ -93,7 +93,7 @@ typedef struct {
                               shape fits), split for the FP64-accurate passes */
   int32_t autotune;        /* 1: before the first solve, time one operator application per
                               candidate launch shape (loads per launch, z stage and tile width,
-                              cluster or split plane passes, y tile width) on this grid and keep
+                              cluster or split plane passes, y tile width and copy form) on this grid and keep
                               the fastest; 0 (default): fixed rules.  When the environment
                               variable HOM_TUNE_CACHE names a file, a shape tuned earlier for the
                               same grid and options is read from it instead of timing again, and a
@@ -125,7 +125,11 @@ typedef struct {
                               6 unit loads of each slot (hom_solve with loads = NULL, n_loads =
                               6 x slots, 0 = all) with CG, BiCGSTAB or the Basic Scheme; hom_effective
                               returns the 6 x (6 x slots) mean stresses, one 6 x 6 block per slot. */
-  int32_t reserved[2];
+  int32_t y_mode;          /* tile copies of the split y pass (FP32 transforms): 0 = per-element
+                              asynchronous copies (the autotuner may pick TMA); 1 = TMA tensor loads
+                              and stores where they fit (an even N1/2 and an even number of spectrum
+                              columns per plane), else as 0.  Results are identical either way. */
+  int32_t reserved[1];
 } hom_options;
 
 typedef struct {
@@ -381,6 +385,11 @@ HOM_API hom_status hom_launch_config(hom_t h, int32_t* loads_per_launch, int32_t
 /* x-y passes of the handle's FP32 transforms: *cluster_ctas = CTAs per plane of the cluster plane
  * passes (hom_options.pass_mode), 0 when the fused plane kernels or the split x and y passes run. */
 HOM_API hom_status hom_plane_config(hom_t h, int32_t* cluster_ctas);
+
+/* split y pass of the handle's iteration passes: *tile_log2 its tile width as log2 of its columns
+ * (-1 when the grid's x-y transforms are not split), *tma = 1 when its FP32 tiles move by TMA tensor
+ * loads and stores (hom_options.y_mode, or the autotuner's pick).  Pointers nullable. */
+HOM_API hom_status hom_ypass_config(hom_t h, int32_t* tile_log2, int32_t* tma);
 
 /* z stage of the handle's iteration passes: *cluster = 1 for the cluster z pass, 2 for its TMA
  * form, 0 for the single-CTA z pass (hom_options.z_mode); *tile_log2 its tile width as log2 of its

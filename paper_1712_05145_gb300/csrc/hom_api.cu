@@ -112,6 +112,7 @@ struct hom_ctx {
   int zc_lg[2] = {-1, -1};     // cluster z-pass tile width forced by the autotuner; -1: rule
   bool zc_off[2] = {false, false};  // the autotuner found the single-CTA z pass faster
   bool zc_tma = false;         // FP32 cluster z pass: the TMA variant (z_mode 2, or the autotuner's pick)
+  bool y_tma = false;          // FP32 split y pass: the TMA variant (y_mode 1, or the autotuner's pick)
   unsigned* d_kerr = nullptr;  // bits set by kernels whose bounded waits gave up
   bool pc_off = false;         // the autotuner found the split x and y passes faster than the cluster ones
   bool tuned = false;
@@ -378,6 +379,17 @@ hom_status timed_launch(hom_ctx* c, int kind, F&& launch) {
   return HOM_OK;
 }
 
+// The split y pass of one chunk: its TMA variant for FP32 transforms where chosen and possible.
+template <typename T>
+cudaError_t ypass(hom_ctx* c, const cx<T>* tw_n2, cx<T>* S, int ncomp, int s_ncomp, int n, int dir,
+                  unsigned long long* yp, const RhsState* st, int rhs0) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->y_tma && ytma_fits(c->g))
+      return launch_ypass_tma(tw_n2, S, c->g, ncomp, s_ncomp, n, dir, yp, st, rhs0, c->d_kerr, c->stream);
+  }
+  return launch_ypass<T>(tw_n2, S, c->g, ncomp, s_ncomp, n, dir, yp, st, rhs0, c->stream);
+}
+
 // Forward x-y transform of one chunk: the fused plane kernel, or the split x and y passes.
 template <typename Tf, typename T>
 hom_status fwd_xy(hom_ctx* c, const FwdArgs<Tf, T>& fa, int n) {
@@ -391,7 +403,7 @@ hom_status fwd_xy(hom_ctx* c, const FwdArgs<Tf, T>& fa, int n) {
   const int yk = sizeof(T) == 8 ? HOM_KERNEL_YPASS_F64 : HOM_KERNEL_YPASS;
   unsigned long long* yp = c->prof_on ? c->d_prof + 2 * yk : nullptr;
   return timed_launch(c, yk, [&] {
-    return launch_ypass<T>(fa.tw_n2, fa.S, c->g, fa.ncomp, fa.ncomp, n, -1, yp, fa.st, fa.rhs0, c->stream);
+    return ypass<T>(c, fa.tw_n2, fa.S, fa.ncomp, fa.ncomp, n, -1, yp, fa.st, fa.rhs0);
   });
 }
 
@@ -407,8 +419,7 @@ hom_status inv_xy(hom_ctx* c, const InvArgs<Tf, T>& ia, int n) {
   const int yk = sizeof(T) == 8 ? HOM_KERNEL_YPASS_F64 : HOM_KERNEL_YPASS;
   unsigned long long* yp = c->prof_on ? c->d_prof + 2 * yk : nullptr;
   CKS(timed_launch(c, yk, [&] {
-    return launch_ypass<T>(ia.tw_n2, const_cast<cx<T>*>(ia.S), c->g, ia.ncomp, ia.s_ncomp, n, +1, yp, ia.st, ia.rhs0,
-                           c->stream);
+    return ypass<T>(c, ia.tw_n2, const_cast<cx<T>*>(ia.S), ia.ncomp, ia.s_ncomp, n, +1, yp, ia.st, ia.rhs0);
   }));
   return timed_launch(c, kind_of<T>(HOM_KERNEL_PLANE_INV), [&] { return launch_xpass_inv<Tf, T>(ia, n, c->stream); });
 }
@@ -617,14 +628,14 @@ hom_status apply_A(hom_ctx* c, int n, const Tf* in, Tf* out, const std::vector<i
 // the split x and y passes; then the split y pass's tile width.  It tunes the passes of the
 // iteration precision T.
 // Tuning cache (HOM_TUNE_CACHE): one line per tuned handle kind,
-//   key: n1 n2 n3 precision transform-bytes z_mode pass_mode n_rve green chunk-capacity
-//   value: chunk zc_off zc_lg ztile_lg pc_off ty_log2 zc_tma
+//   key: n1 n2 n3 precision transform-bytes z_mode pass_mode n_rve green chunk-capacity y_mode
+//   value: chunk zc_off zc_lg ztile_lg pc_off ty_log2 zc_tma y_tma
 // The last line with a matching key wins.  A shape read back is one the tuner itself produced for
 // the same grid and options, so it is valid for this handle.
 std::string tune_key(const hom_ctx* c, size_t tbytes) {
   char b[192];
-  std::snprintf(b, sizeof(b), "%d %d %d %d %zu %d %d %d %d %d", c->g.n1, c->g.n2, c->g.n3, c->opt.precision, tbytes,
-                c->opt.z_mode, c->opt.pass_mode, c->n_rve, c->opt.green_operator, c->chunk);
+  std::snprintf(b, sizeof(b), "%d %d %d %d %zu %d %d %d %d %d %d", c->g.n1, c->g.n2, c->g.n3, c->opt.precision, tbytes,
+                c->opt.z_mode, c->opt.pass_mode, c->n_rve, c->opt.green_operator, c->chunk, c->opt.y_mode);
   return b;
 }
 
@@ -633,12 +644,12 @@ bool tune_cache_load(hom_ctx* c, const char* path, const std::string& key, int i
   if (!f) return false;
   char line[512];
   bool hit = false;
-  int v[7] = {0, 0, 0, 0, 0, 0, 0};
+  int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   while (std::fgets(line, sizeof(line), f)) {
     const char* bar = std::strchr(line, '|');
     if (!bar || std::string(line, (size_t)(bar - line)) != key + " ") continue;
-    int w[7];
-    if (std::sscanf(bar + 1, "%d %d %d %d %d %d %d", &w[0], &w[1], &w[2], &w[3], &w[4], &w[5], &w[6]) == 7) {
+    int w[8];
+    if (std::sscanf(bar + 1, "%d %d %d %d %d %d %d %d", &w[0], &w[1], &w[2], &w[3], &w[4], &w[5], &w[6], &w[7]) == 8) {
       std::memcpy(v, w, sizeof(v));
       hit = true;
     }
@@ -651,15 +662,18 @@ bool tune_cache_load(hom_ctx* c, const char* path, const std::string& key, int i
   c->ztile_lg[idx] = v[3];
   c->pc_off = v[4] != 0;
   if (c->g.split) set_ytile(c->g, v[5]);
-  if (idx == 0) c->zc_tma = v[6] != 0;
+  if (idx == 0) {
+    c->zc_tma = v[6] != 0;
+    c->y_tma = v[7] != 0;
+  }
   return true;
 }
 
 void tune_cache_store(const hom_ctx* c, const char* path, const std::string& key, int idx) {
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s | %d %d %d %d %d %d %d\n", key.c_str(), c->chunk, c->zc_off[idx] ? 1 : 0, c->zc_lg[idx],
-               c->ztile_lg[idx], c->pc_off ? 1 : 0, c->g.ty_log2, c->zc_tma ? 1 : 0);
+  std::fprintf(f, "%s | %d %d %d %d %d %d %d %d\n", key.c_str(), c->chunk, c->zc_off[idx] ? 1 : 0, c->zc_lg[idx],
+               c->ztile_lg[idx], c->pc_off ? 1 : 0, c->g.ty_log2, c->zc_tma ? 1 : 0, c->y_tma ? 1 : 0);
   std::fclose(f);
 }
 
@@ -751,13 +765,24 @@ hom_status autotune(hom_ctx* c) {
     c->zc_lg[idx] = best_lg;
     c->ztile_lg[idx] = -1;
   }
-  // then, where the split y pass runs, its tile width (2^2 .. 2^4 columns) with the rest fixed
+  // then, where the split y pass runs, its tile width (2^2 .. 2^4 columns) and, for FP32
+  // transforms, its tile copies (per-element asynchronous copies or TMA; y_mode 1 keeps TMA) with
+  // the rest fixed
   if (c->g.split && (c->g.pc_Q == 0 || c->pc_off || !std::is_same<T, float>::value)) {
+    constexpr bool f32 = std::is_same<T, float>::value;
     const int lg0 = c->g.ty_log2;
+    const bool tma0 = f32 && c->y_tma;
     int best_y = lg0;
-    for (int lg = 2; lg <= 4; ++lg) {
-      if (lg == lg0 || !ytile_fits(c->g, lg)) continue;
+    bool best_tma = tma0;
+    for (int lg = 2; lg <= 4; ++lg)
+    for (int t = 0; t < 2; ++t) {
+      const bool tma = (t == 1);
+      if (!ytile_fits(c->g, lg) || (lg == lg0 && tma == tma0)) continue;
+      if (tma && !f32) continue;
+      if (f32 && c->opt.y_mode == 1 && !tma) continue;
       set_ytile(c->g, lg);
+      if (tma && !ytma_fits(c->g)) continue;
+      if (f32) c->y_tma = tma;
       CKS(apply_A<T>(c, nt, reinterpret_cast<const T*>(vin), reinterpret_cast<T*>(vout), nullptr));
       CK(cudaEventRecord(e0, c->stream));
       for (int rep = 0; rep < 2; ++rep)
@@ -769,9 +794,11 @@ hom_status autotune(hom_ctx* c) {
       if (ms < best) {
         best = ms;
         best_y = lg;
+        best_tma = tma;
       }
     }
     set_ytile(c->g, best_y);
+    if (f32) c->y_tma = best_tma;
   }
   c->ev_pool.push_back(e0);
   c->ev_pool.push_back(e1);
@@ -1627,6 +1654,14 @@ HOM_API hom_status hom_launch_config(hom_t c, int32_t* loads_per_launch, int32_t
   return HOM_OK;
 }
 
+HOM_API hom_status hom_ypass_config(hom_t c, int32_t* tile_log2, int32_t* tma) {
+  if (!c) return HOM_ERR_ARG;
+  const bool fp32_split = c->fp32 && c->g.split && (c->g.pc_Q == 0 || c->pc_off);
+  if (tile_log2) *tile_log2 = c->g.split ? c->g.ty_log2 : -1;
+  if (tma) *tma = (fp32_split && c->y_tma && ytma_fits(c->g)) ? 1 : 0;
+  return HOM_OK;
+}
+
 HOM_API hom_status hom_plane_config(hom_t c, int32_t* cluster_ctas) {
   if (!c) return HOM_ERR_ARG;
   if (cluster_ctas) *cluster_ctas = (c->g.pc_Q > 0 && !c->pc_off) ? c->g.pc_Q : 0;
@@ -1793,6 +1828,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   const int pass_mode = opt ? opt->pass_mode : 0;
   if (pass_mode < 0 || pass_mode > 3) return HOM_ERR_ARG;
   if (opt && (opt->z_mode < 0 || opt->z_mode > 2)) return HOM_ERR_ARG;
+  if (opt && (opt->y_mode < 0 || opt->y_mode > 1)) return HOM_ERR_ARG;
   if (opt && opt->green_operator != HOM_GREEN_SPECTRAL && opt->green_operator != HOM_GREEN_ROTATED) return HOM_ERR_ARG;
   if (pass_mode == 1 && (long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
 
@@ -1936,6 +1972,7 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if ((s = dalloc(c, (void**)&c->d_kerr, sizeof(unsigned))) != HOM_OK) return bail(s);
   if (cudaMemsetAsync(c->d_kerr, 0, sizeof(unsigned), c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
   c->zc_tma = (c->opt.z_mode == 2);
+  c->y_tma = (c->opt.y_mode == 1);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
   *out = c;
   return HOM_OK;

@@ -172,6 +172,13 @@ cudaError_t launch_xpass_fwd(const FwdArgs<Tf, T>& a, int nrhs, cudaStream_t s);
 template <typename T>
 cudaError_t launch_ypass(const cx<T>* tw_n2, cx<T>* S, const Geo& g, int ncomp, int s_ncomp, int nrhs, int dir,
                          unsigned long long* prof, const RhsState* st, int rhs0, cudaStream_t s);
+// the y pass with its column tiles moved by TMA tensor loads and stores (FP32 transforms); ytma_fits:
+// whether the grid's split y pass can run it (even h and plane, tiles of 2 columns at least); err:
+// nullable word whose bits the kernel sets when its bounded wait gives up (1)
+bool ytma_fits(const Geo& g);
+cudaError_t launch_ypass_tma(const cx<float>* tw_n2, cx<float>* S, const Geo& g, int ncomp, int s_ncomp, int nrhs,
+                             int dir, unsigned long long* prof, const RhsState* st, int rhs0, unsigned* err,
+                             cudaStream_t s);
 template <typename Tf, typename T>
 cudaError_t launch_xpass_inv(const InvArgs<Tf, T>& a, int nrhs, cudaStream_t s);
 template <typename T>

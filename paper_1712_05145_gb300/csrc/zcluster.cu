@@ -258,24 +258,6 @@ bool ztma_fits(const Geo& g, int lg) {
   return lg >= 1 && g.n3 >= 16 && zcluster_tile_fits(g, sizeof(cx<float>), lg) && (g.plane_c % 2) == 0;
 }
 
-namespace {
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-// the driver's tensor-map encoder, found through the runtime (no link against the driver library)
-EncodeTiled encode_tiled() {
-  static const EncodeTiled fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return (EncodeTiled) nullptr;
-    return reinterpret_cast<EncodeTiled>(p);
-  }();
-  return fn;
-}
-}  // namespace
-
 cudaError_t launch_zcluster_tma(const ZArgs<float>& a, int nrhs, cudaStream_t s) {
   const Geo& g = a.g;
   const long long per = (long long)g.n3 << a.tc_log2;
@@ -283,19 +265,16 @@ cudaError_t launch_zcluster_tma(const ZArgs<float>& a, int nrhs, cudaStream_t s)
       per > (long long)kEPT * a.nthr || a.nthr > 512 || a.ntiles < 1 ||
       (reinterpret_cast<uintptr_t>(a.S) & 15) != 0)
     return cudaErrorInvalidValue;
-  const EncodeTiled enc = encode_tiled();
-  if (enc == nullptr) return cudaErrorNotSupported;
   const int nbox = (g.n3 + 255) / 256, rows = g.n3 / nbox;
   const size_t elem = sizeof(cx<float>);
   // the spectra of the launch's loads: [6 nrhs component planes][n3][plane_c] 8-byte elements
   CUtensorMap tm;
-  const cuuint64_t dims[3] = {(cuuint64_t)g.plane_c, (cuuint64_t)g.n3, (cuuint64_t)kZcComps * (cuuint64_t)nrhs};
-  const cuuint64_t strides[2] = {(cuuint64_t)g.plane_c * elem, (cuuint64_t)g.n3 * (cuuint64_t)g.plane_c * elem};
-  const cuuint32_t box[3] = {(cuuint32_t)1 << a.tc_log2, (cuuint32_t)rows, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)a.S, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaErrorInvalidValue;
+  const unsigned long long dims[3] = {(unsigned long long)g.plane_c, (unsigned long long)g.n3,
+                                      (unsigned long long)kZcComps * nrhs};
+  const unsigned long long strides[2] = {(unsigned long long)g.plane_c * elem,
+                                         (unsigned long long)g.n3 * g.plane_c * elem};
+  const unsigned box[2] = {1u << a.tc_log2, (unsigned)rows};
+  if (!encode_tensor_3d(&tm, a.S, dims, strides, box)) return cudaErrorNotSupported;
   const size_t smem = (size_t)(per + g.n3) * elem + 16;
   auto k = zcluster_tma_kernel<kEPT>;
   cudaError_t err = set_smem(k, smem);

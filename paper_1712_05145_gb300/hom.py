@@ -48,7 +48,7 @@ EXPORTED = ["hom_default_options", "hom_create", "hom_solve", "hom_effective", "
             "hom_ls_apply", "hom_equilibrium_error", "hom_fft_forward", "hom_fft_inverse", "hom_green_apply", "hom_profile",
             "hom_profile_read", "hom_ls_apply_noalloc", "hom_noalloc_last_error", "hom_estimate_bytes",
             "hom_server_create", "hom_server_create_batched", "hom_server_counters", "hom_server_submit", "hom_server_poll", "hom_server_wait", "hom_server_stats",
-            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_zpass_config", "hom_plane_config", "hom_set_rve",
+            "hom_server_destroy", "hom_device_bytes", "hom_launch_config", "hom_zpass_config", "hom_ypass_config", "hom_plane_config", "hom_set_rve",
             "hom_launch_count",
             "hom_last_error",
             "hom_status_string", "hom_destroy"]
@@ -60,7 +60,8 @@ class hom_options(ctypes.Structure):
                 ("spectrum_budget_bytes", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
                 ("pass_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("polarization_variant", ctypes.c_int32), ("z_mode", ctypes.c_int32),
-                ("green_operator", ctypes.c_int32), ("n_rve", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("green_operator", ctypes.c_int32), ("n_rve", ctypes.c_int32), ("y_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class hom_solve_info(ctypes.Structure):
@@ -173,6 +174,8 @@ def load_library(path=None):
     lib.hom_set_rve.restype = I32
     lib.hom_plane_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32)]
     lib.hom_plane_config.restype = ctypes.c_int
+    lib.hom_ypass_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.hom_ypass_config.restype = ctypes.c_int
     lib.hom_zpass_config.argtypes = [V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.hom_zpass_config.restype = ctypes.c_int
     lib.hom_launch_count.argtypes = []
@@ -416,6 +419,13 @@ def hom_plane_config(h):
     return a.value
 
 
+def hom_ypass_config(h):
+    """(tile log2 width or -1, 1 if its FP32 tiles move by TMA else 0) of a handle's split y pass."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(h, load_library().hom_ypass_config(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def hom_zpass_config(h):
     """(z stage, tile log2 width or -1) of a handle's iteration passes; the z stage is 1 for the
     cluster z pass, 2 for its TMA form, 0 for the single-CTA z pass."""
@@ -446,7 +456,8 @@ class Homogenization:
 
     def __init__(self, ms, precision=HOM_FP32_REFINE, scheme=HOM_CG, max_iter=2000, check_every=8,
                  max_refine=6, rhs_chunk=0, spectrum_budget_bytes=1024 << 20, stream=None, lam0=None, mu0=None,
-                 pass_mode=0, autotune=0, polarization_variant=0, z_mode=0, green_operator=0, n_rve=1):
+                 pass_mode=0, autotune=0, polarization_variant=0, z_mode=0, green_operator=0, n_rve=1,
+                 y_mode=0):
         n3, n2, n1 = ms.phase.shape
         self.grid = (n1, n2, n3)
         self.M = n1 * n2 * n3
@@ -465,6 +476,7 @@ class Homogenization:
         opt.z_mode = z_mode
         opt.green_operator = green_operator
         opt.n_rve = n_rve
+        opt.y_mode = y_mode
         self.h = hom_create(self.grid, ms.phase, ms.lame, ms.lam0 if lam0 is None else lam0,
                             ms.mu0 if mu0 is None else mu0, opt)
         self.nloads = {}

@@ -4,7 +4,7 @@ Runs a few CG iterations of the order-0 problem and stops at the iteration cap, 
 sees every LS-step kernel kind with a small, fixed number of launches.  The default is the
 benchmark microstructure (128^3 random spheres, 6 load cases, FP32 fields); --shape gives any
 grid (the same generator, scaled to the grid), --loads the number of unit loads, and --pass-mode /
---z-mode select the plane and z passes (hom_options.pass_mode, z_mode).  --autotune tunes the
+--z-mode / --y-mode select the plane, z and y passes (hom_options.pass_mode, z_mode, y_mode).  --autotune tunes the
 launch shape in a first solve and profiles a second one:
 
     python -m paper_1712_05145_gb300.profile_case --grid 128 --iters 2
@@ -23,6 +23,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--pass-mode", type=int, default=0)
     ap.add_argument("--z-mode", type=int, default=0)
+    ap.add_argument("--y-mode", type=int, default=0)
     ap.add_argument("--seed", type=int, default=1713)
     ap.add_argument("--times", action="store_true", help="print per-kernel device times (CUDA events)")
     ap.add_argument("--autotune", action="store_true", help="tune the launch shape first (hom_options.autotune)")
@@ -37,7 +38,7 @@ def main():
     prec = hom.HOM_FP32_REFINE if args.precision == "fp32" else hom.HOM_FP64
     H = hom.Homogenization(ms, precision=prec, scheme=hom.HOM_CG, max_iter=args.iters,
                            check_every=args.iters, max_refine=0, pass_mode=args.pass_mode, z_mode=args.z_mode,
-                           autotune=1 if args.autotune else 0)
+                           y_mode=args.y_mode, autotune=1 if args.autotune else 0)
     if args.autotune:
         H.solve(0, 1e-6, loads=np.eye(6)[: args.loads])
     if args.times:
@@ -45,7 +46,8 @@ def main():
     info = H.solve(0, 1e-6, loads=np.eye(6)[: args.loads])
     torch.cuda.synchronize()
     out = {"grid": list(grid), "iters": [i["iterations"] for i in info],
-           "plane_cluster_ctas": hom.hom_plane_config(H.h), "zpass_cluster_tile": hom.hom_zpass_config(H.h)}
+           "plane_cluster_ctas": hom.hom_plane_config(H.h), "zpass_cluster_tile": hom.hom_zpass_config(H.h),
+           "ypass_tile_tma": hom.hom_ypass_config(H.h)}
     if args.times:
         out["kernels"] = [{"kernel": p["kernel"], "launches": p["launches"],
                            "ms_per_launch": p["ms"] / p["launches"], "gbs": p["bytes"] / (p["ms"] / 1e3) / 1e9}
