@@ -368,7 +368,8 @@ def main():
     barrier()
     clk = clocks.stop()
     launch_shape = {"loads_per_launch": hom.hom_launch_config(H.h)[0], "plane_cluster_ctas": hom.hom_plane_config(H.h),
-                    "zpass_cluster_tile_log2": list(hom.hom_zpass_config(H.h))}
+                    "zpass_cluster_tile_log2": list(hom.hom_zpass_config(H.h)),
+                    "ypass_tile_log2_tma": list(hom.hom_ypass_config(H.h))}
     info = r["info"]
     total_ms, job_vi = replicas.aggregate(r["total_ms"], float(M) * r["iters"], device="cuda")
     value = job_vi / (total_ms / 1e3)
@@ -410,7 +411,7 @@ def main():
             "ceff_rel_err_vs_oracle": rel_err(r2["c_eff"], g2["c_eff"]) if g2 else None,
             "roofline": roof2, "roofline_kernel_io": io2, "ls_step": ls2, "kernels": r2["prof"],
             "launch_shape": {"loads_per_launch": hom.hom_launch_config(H2.h)[0],
-                             "zpass_cluster_tile_log2": hom.hom_zpass_config(H2.h)}}
+                             "zpass_cluster_tile_log2": list(hom.hom_zpass_config(H2.h))}}
         H2.close()
 
     if not args.no_extras and not args.no_serving:

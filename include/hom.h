@@ -103,13 +103,15 @@ typedef struct {
                               which also converges where a phase modulus is 0) */
   int32_t z_mode;          /* z stage of the LS step: 0 = cluster z pass (six CTAs, one per Kelvin
                               component, meeting in distributed shared memory for the Green
-                              contraction) where its tile fits, else the single-CTA z pass (the
-                              autotuner may pick any of the three forms);
+                              contraction) where its tile fits, else the single-CTA z pass; for FP32
+                              transforms its tiles move by TMA tensor loads and stores where that
+                              fits (N3 >= 16, an even number of spectrum columns per plane); the
+                              autotuner may pick any of these forms;
                               1 = always the single-CTA z pass (three passes on deep grids);
-                              2 = the cluster z pass with its tiles moved by TMA tensor loads and
-                              stores where that fits (FP32 transforms, N3 >= 16, an even number of
-                              spectrum columns per plane), else as 0.  Results are identical to
-                              those of 0 with the same tile width. */
+                              2 = the cluster z pass in its TMA form where that fits, else as 0;
+                              3 = the cluster z pass with per-element asynchronous copies where its
+                              tile fits, else as 0.  The two copy forms give identical results for
+                              the same tile width. */
   int32_t green_operator;  /* HOM_GREEN_SPECTRAL (0): Gamma0_hat of Sec. 2 at the discrete wave
                               vector (Nyquist components 0).  HOM_GREEN_ROTATED (1): the Green
                               operator of the rotated finite-difference discretisation (corner
@@ -125,10 +127,11 @@ typedef struct {
                               6 unit loads of each slot (hom_solve with loads = NULL, n_loads =
                               6 x slots, 0 = all) with CG, BiCGSTAB or the Basic Scheme; hom_effective
                               returns the 6 x (6 x slots) mean stresses, one 6 x 6 block per slot. */
-  int32_t y_mode;          /* tile copies of the split y pass (FP32 transforms): 0 = per-element
-                              asynchronous copies (the autotuner may pick TMA); 1 = TMA tensor loads
+  int32_t y_mode;          /* tile copies of the split y pass (FP32 transforms): 0 = TMA tensor loads
                               and stores where they fit (an even N1/2 and an even number of spectrum
-                              columns per plane), else as 0.  Results are identical either way. */
+                              columns per plane), else per-element asynchronous copies; the
+                              autotuner may pick either; 1 = TMA where it fits, kept by the
+                              autotuner; 2 = per-element copies.  Results are identical. */
   int32_t reserved[1];
 } hom_options;
 
@@ -388,7 +391,7 @@ HOM_API hom_status hom_plane_config(hom_t h, int32_t* cluster_ctas);
 
 /* split y pass of the handle's iteration passes: *tile_log2 its tile width as log2 of its columns
  * (-1 when the grid's x-y transforms are not split), *tma = 1 when its FP32 tiles move by TMA tensor
- * loads and stores (hom_options.y_mode, or the autotuner's pick).  Pointers nullable. */
+ * loads and stores (hom_options.y_mode and the autotuner's pick).  Pointers nullable. */
 HOM_API hom_status hom_ypass_config(hom_t h, int32_t* tile_log2, int32_t* tma);
 
 /* z stage of the handle's iteration passes: *cluster = 1 for the cluster z pass, 2 for its TMA

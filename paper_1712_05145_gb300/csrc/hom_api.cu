@@ -111,8 +111,8 @@ struct hom_ctx {
   int ztile_lg[2] = {-1, -1};  // z-pass tile width forced by the autotuner (FP32, FP64); -1: rule
   int zc_lg[2] = {-1, -1};     // cluster z-pass tile width forced by the autotuner; -1: rule
   bool zc_off[2] = {false, false};  // the autotuner found the single-CTA z pass faster
-  bool zc_tma = false;         // FP32 cluster z pass: the TMA variant (z_mode 2, or the autotuner's pick)
-  bool y_tma = false;          // FP32 split y pass: the TMA variant (y_mode 1, or the autotuner's pick)
+  bool zc_tma = false;         // FP32 cluster z pass: the TMA form (z_mode 0 and 2, or the autotuner's pick)
+  bool y_tma = false;          // FP32 split y pass: the TMA form (y_mode 0 and 1, or the autotuner's pick)
   unsigned* d_kerr = nullptr;  // bits set by kernels whose bounded waits gave up
   bool pc_off = false;         // the autotuner found the split x and y passes faster than the cluster ones
   bool tuned = false;
@@ -690,8 +690,9 @@ hom_status autotune(hom_ctx* c) {
   for (int k : {1, 2, 3, 4, 6, 8, 12})
     if (k <= nt) chunks.push_back(k);
   // z-stage candidates: (0, lg) the single-CTA z pass with 2^lg columns, (1, lg) the cluster z
-  // pass, (2, lg) its TMA variant (FP32 transforms).  z_mode 2 keeps the TMA variant where it fits.
-  std::vector<std::pair<int, int>> zcand, ztma;
+  // pass with per-element copies, (2, lg) its TMA form (FP32 transforms).  z_mode 1 keeps the
+  // single-CTA pass, 2 the TMA form and 3 the per-element form where they fit.
+  std::vector<std::pair<int, int>> zcand, zplain, ztma;
   for (int lg = 0; lg <= 4; ++lg)
     if (zpass_tile_fits(c->g, sizeof(cx<T>), 6, lg)) zcand.push_back({0, lg});
   if (c->opt.z_mode != 1) {
@@ -699,13 +700,19 @@ hom_status autotune(hom_ctx* c) {
       ZArgs<T> probe{};
       probe.g = c->g;
       if (((size_t)1 << lg) * sizeof(cx<T>) >= 32 && zcluster_tiling<T>(probe, lg) && probe.tc_log2 == lg) {
-        if (c->opt.z_mode == 0) zcand.push_back({1, lg});
+        zplain.push_back({1, lg});
         if (std::is_same<T, float>::value && ztma_fits(c->g, lg)) ztma.push_back({2, lg});
       }
     }
   }
-  if (c->opt.z_mode == 2 && !ztma.empty()) zcand = ztma;
-  else zcand.insert(zcand.end(), ztma.begin(), ztma.end());
+  if (c->opt.z_mode == 2 && !ztma.empty()) {
+    zcand = ztma;
+  } else if ((c->opt.z_mode == 3 || (c->opt.z_mode == 2 && !std::is_same<T, float>::value)) && !zplain.empty()) {
+    zcand = zplain;
+  } else {
+    zcand.insert(zcand.end(), zplain.begin(), zplain.end());
+    zcand.insert(zcand.end(), ztma.begin(), ztma.end());
+  }
   if (zcand.empty()) return HOM_OK;
   const size_t fb = tbytes<T>(c, nt, 6);
   void *vin, *vout;
@@ -779,7 +786,7 @@ hom_status autotune(hom_ctx* c) {
       const bool tma = (t == 1);
       if (!ytile_fits(c->g, lg) || (lg == lg0 && tma == tma0)) continue;
       if (tma && !f32) continue;
-      if (f32 && c->opt.y_mode == 1 && !tma) continue;
+      if (f32 && ((c->opt.y_mode == 1 && !tma) || (c->opt.y_mode == 2 && tma))) continue;
       set_ytile(c->g, lg);
       if (tma && !ytma_fits(c->g)) continue;
       if (f32) c->y_tma = tma;
@@ -1827,8 +1834,8 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
     return HOM_ERR_SIZE;
   const int pass_mode = opt ? opt->pass_mode : 0;
   if (pass_mode < 0 || pass_mode > 3) return HOM_ERR_ARG;
-  if (opt && (opt->z_mode < 0 || opt->z_mode > 2)) return HOM_ERR_ARG;
-  if (opt && (opt->y_mode < 0 || opt->y_mode > 1)) return HOM_ERR_ARG;
+  if (opt && (opt->z_mode < 0 || opt->z_mode > 3)) return HOM_ERR_ARG;
+  if (opt && (opt->y_mode < 0 || opt->y_mode > 2)) return HOM_ERR_ARG;
   if (opt && opt->green_operator != HOM_GREEN_SPECTRAL && opt->green_operator != HOM_GREEN_ROTATED) return HOM_ERR_ARG;
   if (pass_mode == 1 && (long long)(n1 / 2) * n2 > 8192) return HOM_ERR_SIZE;
 
@@ -1971,8 +1978,8 @@ HOM_API hom_status hom_create(const int32_t grid[3], const uint8_t* phase, int32
   if ((s = ensure_cap(c, 6)) != HOM_OK) return bail(s);
   if ((s = dalloc(c, (void**)&c->d_kerr, sizeof(unsigned))) != HOM_OK) return bail(s);
   if (cudaMemsetAsync(c->d_kerr, 0, sizeof(unsigned), c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
-  c->zc_tma = (c->opt.z_mode == 2);
-  c->y_tma = (c->opt.y_mode == 1);
+  c->zc_tma = (c->opt.z_mode == 0 || c->opt.z_mode == 2);
+  c->y_tma = (c->opt.y_mode != 2);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(HOM_ERR_CUDA);
   *out = c;
   return HOM_OK;

@@ -58,12 +58,12 @@ def test_fused_only_mode_rejects_planes_larger_than_one_cta(lib):
         hom.hom_create((8, 8, 8), np.zeros((8, 8, 8), np.uint8), np.array([[1.0, 1.0]]), 1.0, 1.0, opt)
     assert e.value.status == hom.HOM_ERR_ARG
     opt.pass_mode = 0
-    opt.z_mode = 3
+    opt.z_mode = 4
     with pytest.raises(hom.HomError) as e:
         hom.hom_create((8, 8, 8), np.zeros((8, 8, 8), np.uint8), np.array([[1.0, 1.0]]), 1.0, 1.0, opt)
     assert e.value.status == hom.HOM_ERR_ARG
     opt.z_mode = 0
-    opt.y_mode = 2
+    opt.y_mode = 3
     with pytest.raises(hom.HomError) as e:
         hom.hom_create((8, 8, 8), np.zeros((8, 8, 8), np.uint8), np.array([[1.0, 1.0]]), 1.0, 1.0, opt)
     assert e.value.status == hom.HOM_ERR_ARG

@@ -26,15 +26,15 @@ def cases():
 CASES = list(cases())
 
 
-@pytest.mark.parametrize("z_mode", [0, 1, 2])
+@pytest.mark.parametrize("z_mode", [0, 1, 3])
 @pytest.mark.parametrize("pass_mode", [0, 2, 3])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name,ms", CASES, ids=[c[0] for c in CASES])
 def test_ls_step_matches_oracle(name, ms, precision, pass_mode, z_mode):
     """Fused plane kernels (pass_mode 0 on these grids), split x / y passes (pass_mode 2) and
     cluster plane passes (pass_mode 3, FP32 transforms); the cluster z pass (z_mode 0, on grids
-    with N3 >= 16), the single-CTA z pass (z_mode 1) and the cluster z pass with TMA tile copies
-    (z_mode 2, FP32 transforms on grids with N3 >= 16 and an even number of spectrum columns)."""
+    with N3 >= 16; TMA tile copies for FP32 transforms where they fit), the single-CTA z pass
+    (z_mode 1) and the cluster z pass with per-element copies (z_mode 3)."""
     from paper_1712_05145_gb300 import hom
     if pass_mode == 3 and precision == 1 and (ms.grid[0] // 2) % 2:
         with pytest.raises(hom.HomError):   # no cluster of 2, 4 or 8 divides an odd N1/2
@@ -109,13 +109,13 @@ def deep_grid_case():
     return ms, eps, E, ref, sols
 
 
-@pytest.mark.parametrize("z_mode", [0, 1, 2])
+@pytest.mark.parametrize("z_mode", [0, 1, 3])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_split_z_stage_on_deep_grid(deep_grid_case, precision, z_mode):
     """N3 = 512: with the single-CTA z pass (z_mode 1) the fused z tiles would be narrower than a
     sector, so the z stage runs as per-component z FFTs and a pointwise contraction; the cluster z
-    pass (z_mode 0, and its TMA form, z_mode 2) keeps it one pass.  LS step and solve against the
-    oracle."""
+    pass (z_mode 0 in its TMA form for FP32, z_mode 3 with per-element copies) keeps it one pass.
+    LS step and solve against the oracle."""
     from paper_1712_05145_gb300 import hom
     ms, eps, E, ref, sols = deep_grid_case
     H = hom.Homogenization(ms, precision=precision, z_mode=z_mode)

@@ -1,5 +1,5 @@
-"""TMA tile copies in the split y pass (hom_options.y_mode = 1) and the cluster z pass (z_mode = 2),
-FP32 transforms.
+"""TMA tile copies in the split y pass (hom_options.y_mode 0 and 1) and the cluster z pass (z_mode 0
+and 2), FP32 transforms, against the per-element copies (y_mode 2, z_mode 3).
 
 The z stage of the LS step (Sec. 2: the transform along z, eta_hat = -Gamma0_hat(xi) : tau_hat with
 eta_hat(0) = 0, the inverse transform) runs the same arithmetic as the plain cluster z pass, with
@@ -49,13 +49,10 @@ def test_ls_step_matches_oracle_and_plain_cluster_bits(grid, kind):
     E = np.random.default_rng(9).uniform(-1, 1, size=(nrhs, 6))
     ref = np.stack([oracle_ls_step_mandel(pb, eps[i], E[i]) for i in range(nrhs)])
     outs = {}
-    for z_mode in (2, 0):
+    for z_mode in (2, 3, 0):
         H = hom.Homogenization(ms, precision=1, z_mode=z_mode)
         cluster, lg = _config(H)
-        if z_mode == 2:
-            assert cluster == kind, (cluster, lg)
-        else:
-            assert cluster == 1
+        assert cluster == (1 if z_mode == 3 else kind), (z_mode, cluster, lg)
         ed = torch.from_numpy(eps).cuda()
         out = torch.empty_like(ed)
         hom.hom_ls_apply(H.h, nrhs, ed, E, out)
@@ -63,7 +60,8 @@ def test_ls_step_matches_oracle_and_plain_cluster_bits(grid, kind):
         H.close()
     assert rel_err(outs[2], ref) < TOL[1]
     # same tile width, same FFT and contraction code: the same bits
-    assert np.array_equal(outs[2], outs[0])
+    assert np.array_equal(outs[2], outs[3])
+    assert np.array_equal(outs[0], outs[2])
 
 
 def test_solve_bits_and_autotuned_width():
@@ -73,20 +71,20 @@ def test_solve_bits_and_autotuned_width():
     ms = _ms((32, 24, 128), 4)
     loads = np.eye(6)
     res = {}
-    for z_mode in (2, 0):
+    for z_mode in (2, 3):
         H = hom.Homogenization(ms, precision=1, z_mode=z_mode)
         info = H.solve(0, 1e-6, loads=loads)
         assert all(i["status"] == 0 for i in info), info
         res[z_mode] = (H.effective(0), np.stack([H.field(0, k) for k in range(6)]))
         H.close()
-    assert np.array_equal(res[2][0], res[0][0])
-    assert np.array_equal(res[2][1], res[0][1])
+    assert np.array_equal(res[2][0], res[3][0])
+    assert np.array_equal(res[2][1], res[3][1])
     H = hom.Homogenization(ms, precision=1, z_mode=2, autotune=1)
     info = H.solve(0, 1e-6, loads=loads)
     assert all(i["status"] == 0 for i in info), info
     cluster, lg = _config(H)
     assert cluster == 2 and 1 <= lg <= 6, (cluster, lg)
-    assert rel_err(H.effective(0), res[0][0]) < 1e-5
+    assert rel_err(H.effective(0), res[3][0]) < 1e-5
     H.close()
 
 
@@ -127,18 +125,19 @@ def test_y_pass_ls_step_matches_oracle_and_plain_bits(grid, tma):
     E = np.random.default_rng(19).uniform(-1, 1, size=(nrhs, 6))
     ref = np.stack([oracle_ls_step_mandel(pb, eps[i], E[i]) for i in range(nrhs)])
     outs = {}
-    for y_mode in (1, 0):
+    for y_mode in (1, 2, 0):
         H = hom.Homogenization(ms, precision=1, pass_mode=2, y_mode=y_mode)
         lg, used = _yconfig(H)
         assert lg >= 0
-        assert used == (tma if y_mode == 1 else 0), (lg, used)
+        assert used == (0 if y_mode == 2 else tma), (y_mode, lg, used)
         ed = torch.from_numpy(eps).cuda()
         out = torch.empty_like(ed)
         hom.hom_ls_apply(H.h, nrhs, ed, E, out)
         outs[y_mode] = out.cpu().numpy()
         H.close()
     assert rel_err(outs[1], ref) < TOL[1]
-    assert np.array_equal(outs[1], outs[0])
+    assert np.array_equal(outs[1], outs[2])
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_y_and_z_tma_solve_bits_and_autotune():
@@ -148,16 +147,16 @@ def test_y_and_z_tma_solve_bits_and_autotune():
     ms = _ms((64, 48, 32), 6)
     loads = np.eye(6)[[0, 2, 4]]
     res = {}
-    for modes in ((1, 2), (0, 0)):
+    for modes in ((1, 2), (2, 3)):
         H = hom.Homogenization(ms, precision=1, pass_mode=2, y_mode=modes[0], z_mode=modes[1])
-        assert _yconfig(H)[1] == modes[0]
+        assert _yconfig(H)[1] == (1 if modes[0] == 1 else 0)
         assert _config(H)[0] == (2 if modes[1] == 2 else 1)
         info = H.solve(0, 1e-6, loads=loads)
         assert all(i["status"] == 0 for i in info), info
         res[modes] = (H.effective(0), np.stack([H.field(0, k) for k in range(3)]))
         H.close()
-    assert np.array_equal(res[(1, 2)][0], res[(0, 0)][0])
-    assert np.array_equal(res[(1, 2)][1], res[(0, 0)][1])
+    assert np.array_equal(res[(1, 2)][0], res[(2, 3)][0])
+    assert np.array_equal(res[(1, 2)][1], res[(2, 3)][1])
     H = hom.Homogenization(ms, precision=1, pass_mode=2, y_mode=1, autotune=1)
     info = H.solve(0, 1e-6, loads=loads)
     assert all(i["status"] == 0 for i in info), info
