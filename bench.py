@@ -113,10 +113,11 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "plane_fwd": ["plane_fwd.cu", "plane_cluster.cu", "xpass.cu"],
     "plane_fwd_f64": ["plane_fwd.cu", "xpass.cu"],
-    "zpass": ["zpass.cu", "zcluster.cu", "spectral.cuh"], "zpass_f64": ["zpass.cu", "zcluster.cu", "spectral.cuh"],
+    "zpass": ["zpass.cu", "zcluster.cu", "spectral.cuh", "tma.cuh"],
+    "zpass_f64": ["zpass.cu", "zcluster.cu", "spectral.cuh", "tma.cuh"],
     "plane_inv": ["plane_inv.cu", "plane_cluster.cu", "xpass.cu"],
     "plane_inv_f64": ["plane_inv.cu", "xpass.cu"],
-    "ypass": ["ypass.cu"], "ypass_f64": ["ypass.cu"],
+    "ypass": ["ypass.cu", "tma.cuh"], "ypass_f64": ["ypass.cu", "tma.cuh"],
 }
 KERNEL_HEADERS = ["ls_common.cuh", "common.cuh", "internal.h"]
 
