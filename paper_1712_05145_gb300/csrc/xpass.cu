@@ -11,8 +11,10 @@ namespace hom {
 
 // FP32 forward x pass: at most 64 registers, so four 256-thread CTAs fit an SM (74 registers and
 // three CTAs without the bound); the extra resident warps hide its field loads (512^3: 3.65 ->
-// 3.39 ms per launch), without spills.  The FP64 and double-float forms keep their registers.
-template <typename T> struct XfCfg { static constexpr int kMinBlocks = 1; };
+// 3.39 ms per launch), without spills.  The FP64 and double-float forms: at most 128 registers,
+// two CTAs per SM (with a bound of one CTA the double-float form takes 156 registers and runs 30 %
+// slower).
+template <typename T> struct XfCfg { static constexpr int kMinBlocks = 2; };
 template <> struct XfCfg<float> { static constexpr int kMinBlocks = 4; };
 
 template <typename Tf, typename T, int EPT>
