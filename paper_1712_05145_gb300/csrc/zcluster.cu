@@ -118,8 +118,9 @@ __global__ void __cluster_dims__(kZcComps, 1, 1) __launch_bounds__(512, ZcCfg<T>
 // tensor loads of the CTA's component (one box per 256 z-planes), which complete on an mbarrier,
 // and after the inverse FFTs the tensor stores.  Columns past the plane read as zero and are not
 // written.  Several CTAs per SM overlap one tile's copies with other tiles' FFTs.  (A persistent
-// form that loops over tiles measured worse at compile time already: the FFT stages' thread-
-// invariant indexes of every length stay live across the loop and spill.)
+// form that loops over tiles, loading the next tile during the current one, spills: inside the
+// loop the compiler keeps the FFT stages' thread-invariant indexes of every length live, about
+// 8 KB of stack per thread.)
 constexpr unsigned long long kZtWaitNs = 2000000000ull;  // a tile load that takes 2 s is an error
 
 template <int EPT>
