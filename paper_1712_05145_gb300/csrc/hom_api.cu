@@ -2177,7 +2177,7 @@ hom_status fft_fwd_impl(hom_ctx* c, int nf, const double* f, double* fhat) {
   CK(launch_zpass<T>(za, nf, c->stream));
   CK(launch_spec_to_std<T>((const cx<T>*)vs, fhat, c->g, 1, nf, 0, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  return HOM_OK;
+  return check_kernel_flags(c);   // the split y pass may run in its TMA form
 }
 template <typename T>
 hom_status fft_inv_impl(hom_ctx* c, int nf, const double* fhat, double* f) {
@@ -2196,7 +2196,7 @@ hom_status fft_inv_impl(hom_ctx* c, int nf, const double* fhat, double* f) {
   CKS((inv_xy<T, T>(c, ia, 1)));
   CK((launch_convert<T, double>((const T*)vout, f, (long long)nf * c->g.M, c->stream)));
   CK(cudaStreamSynchronize(c->stream));
-  return HOM_OK;
+  return check_kernel_flags(c);   // the split y pass may run in its TMA form
 }
 template <typename T>
 hom_status green_impl(hom_ctx* c, int nrhs, const double* th, double* eh) {
